@@ -1,0 +1,54 @@
+"""FP64 CPU oracle for approximate-ordering VarLiNGAM (test infrastructure).
+
+This package is test infrastructure.  Only the test-suite, the smoke check and
+the timed CPU baseline of the benchmark may import it; the library's CUDA path
+never does, and nothing here imports the library.  It is deliberately plain and
+slow: float64 NumPy, one obvious loop per step of the paper, no blocking, no
+fusion and no incremental tricks, so that a reader can check it against the
+paper by eye.
+
+Contents (all in :mod:`oracle.fp64`):
+
+* ``var_ols``            VAR(p) least squares with intercept (Section 4.1).
+* ``standardize``        zero mean, unit variance per variable (Section 3, step 1).
+* ``entropy``            maximum-entropy approximation H(u) (Section 3, step 3;
+                         the constants are pinned in ``entropy_constants``).
+* ``pairwise_measure``   E_x, E_r and the likelihood-ratio matrix D
+                         (Section 3 steps 2-3, Eqs. 1-2; Section 4.2 items 1-2).
+* ``order_heuristic``    Algorithm 1: m greedy argmins of Eq. 3 over the static
+                         precomputed tables.
+* ``order_standard``     the iterative DirectLiNGAM search with the data
+                         refinement of Eq. 4 (Section 3, steps 1-5).
+* ``b0_ols`` / ``b0_ldl`` two independent routes to B0 from a causal order.
+* ``btau``               B_tau = (I - B0) M_tau.
+* ``varlingam``          the whole pipeline, heuristic or standard.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+against closed forms, quadrature, brute force or library routines, except the
+literature constant k1 = 79.047 of ``entropy`` (reproduced to 4 digits by a
+quadrature in the tests, see ``entropy_constants``) and the accuracy of the
+heuristic relative to the standard method, which is reported, not asserted
+("parity unpinned": the paper gives no worked example of it).
+"""
+from .fp64 import (  # noqa: F401
+    ENTROPY_GAMMA,
+    ENTROPY_K1,
+    ENTROPY_K2,
+    H_GAUSS,
+    b0_ldl,
+    b0_ols,
+    btau,
+    entropy,
+    logcosh,
+    order_gap_ok,
+    order_heuristic,
+    order_standard,
+    pairwise_measure,
+    relative_gap,
+    residual,
+    score,
+    scores_over,
+    standardize,
+    var_ols,
+    varlingam,
+)

@@ -1,0 +1,301 @@
+"""Plain FP64 restatement of approximate-ordering VarLiNGAM (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU baseline use this
+module.  Every function names the passage of the paper it follows.  Where the
+paper is silent (the entropy formula, the aggregation function f, B0 and B_tau
+estimation, the VAR details) the reading used is stated in the docstring; the
+readings come from the two methods the paper builds on, DirectLiNGAM
+(Shimizu et al. 2011) and VarLiNGAM (Hyvarinen et al. 2010).
+
+Conventions: data matrices are variable-major, X[i, t] = variable i at time t.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.linalg
+
+# ------------------------------------------------------------------ entropy
+# Maximum-entropy approximation of differential entropy (Hyvarinen 1998) with
+# the two contrast functions G1(u) = log cosh u and G2(u) = u exp(-u^2/2), the
+# form DirectLiNGAM uses.  The paper only says "an entropy approximation"
+# (Section 3, step 3).
+H_GAUSS = 0.5 * (1.0 + math.log(2.0 * math.pi))  # entropy of N(0, 1)
+ENTROPY_K1 = 79.047  # weight of (E log cosh u - gamma)^2 (literature value)
+ENTROPY_K2 = 7.4129  # weight of (E u exp(-u^2/2))^2 (= 36 / (8 sqrt3 - 9))
+ENTROPY_GAMMA = 0.37457  # E log cosh nu for nu ~ N(0, 1)
+
+
+def logcosh(u: np.ndarray) -> np.ndarray:
+    """log cosh u = log((e^u + e^-u) / 2), evaluated without overflow."""
+    return np.logaddexp(u, -u) - math.log(2.0)
+
+
+def entropy(u: np.ndarray) -> float:
+    """H(u) = H_nu - k1 (E[log cosh u] - gamma)^2 - k2 (E[u exp(-u^2/2)])^2
+    for a standardized sample u (Section 3, step 3; formula is the reading
+    above)."""
+    u = np.asarray(u, dtype=np.float64)
+    a = np.mean(logcosh(u))
+    b = np.mean(u * np.exp(-0.5 * u * u))
+    return H_GAUSS - ENTROPY_K1 * (a - ENTROPY_GAMMA) ** 2 - ENTROPY_K2 * b ** 2
+
+
+# ------------------------------------------------------------------ VAR fit
+def var_ols(X: np.ndarray, p: int) -> Tuple[np.ndarray, np.ndarray]:
+    """VAR(p) least-squares fit x_t = c + sum_tau M_tau x_{t-tau} + n_t
+    (Section 2.1 and Section 4.1: VarLiNGAM first fits a VAR and hands its
+    residuals, the instantaneous shocks, to LiNGAM).
+
+    Reading: an intercept c is fitted (as a VAR fit of a series with unknown
+    mean does); rows t = p .. n-1 are the n_eff = n - p equations.
+
+    Returns M (p, m, m) with M[tau-1][i, k] the effect of x_k(t - tau) on
+    x_i(t), and the residuals E (m, n_eff), E[:, s] = n_{p+s}.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    n_eff = n - p
+    if n_eff <= m * p + 1:
+        raise ValueError("VAR system has no unique least-squares solution")
+    Y = X[:, p:].T  # (n_eff, m)
+    cols = [X[:, p - tau:n - tau].T for tau in range(1, p + 1)]
+    Z = np.hstack(cols + [np.ones((n_eff, 1))])  # (n_eff, m p + 1)
+    coef, *_ = np.linalg.lstsq(Z, Y, rcond=None)  # (m p + 1, m)
+    M = np.stack([coef[(tau - 1) * m:tau * m, :].T for tau in range(1, p + 1)])
+    E = (Y - Z @ coef).T
+    return M, np.ascontiguousarray(E)
+
+
+# ------------------------------------------------------ pairwise measure
+def standardize(X: np.ndarray) -> np.ndarray:
+    """Zero mean and unit variance per variable (Section 3, step 1), with the
+    population standard deviation (ddof = 0)."""
+    X = np.asarray(X, dtype=np.float64)
+    mu = X.mean(axis=1, keepdims=True)
+    sd = X.std(axis=1, keepdims=True)
+    return (X - mu) / sd
+
+
+def residual(xi: np.ndarray, xj: np.ndarray) -> np.ndarray:
+    """Eq. 1: r_{i<-j} = x_i - cov(x_i, x_j) / var(x_j) * x_j (ddof 0 for both,
+    so the ratio is the least-squares slope)."""
+    ci = xi - xi.mean()
+    cj = xj - xj.mean()
+    cov = np.mean(ci * cj)
+    var = np.mean(cj * cj)
+    return xi - (cov / var) * xj
+
+
+def pairwise_measure(Xs: np.ndarray) -> Dict[str, np.ndarray]:
+    """One-time precomputation of Section 4.2 (items 1-2; Algorithm 1, the two
+    precompute calls) on the standardized data Xs (m, n).
+
+    E_x[i]    = H(x_i)                              (variable entropies)
+    E_r[i, j] = H(r_{i<-j} / std(r_{i<-j}))         (residual entropies)
+    T[i, j]   = T_{i<-j} = E_x[i] - E_r[i, j]       (Eq. 2)
+    D[i, j]   = T_{j<-i} - T_{i<-j}
+              = E_x[j] + E_r[i, j] - E_x[i] - E_r[j, i]
+
+    Reading: each residual is rescaled to unit variance before H, because the
+    approximation of H holds for standardized variables (DirectLiNGAM does the
+    same).  D[i, j] > 0 is evidence for i -> j.  Diagonals are zero.
+    """
+    Xs = np.asarray(Xs, dtype=np.float64)
+    m, _ = Xs.shape
+    Ex = np.array([entropy(Xs[i]) for i in range(m)])
+    Er = np.zeros((m, m))
+    for i in range(m):
+        for j in range(m):
+            if i == j:
+                continue
+            r = residual(Xs[i], Xs[j])
+            Er[i, j] = entropy(r / r.std())
+    T = Ex[:, None] - Er
+    np.fill_diagonal(T, 0.0)
+    D = T.T - T
+    return {"Ex": Ex, "Er": Er, "T": T, "D": D}
+
+
+# ------------------------------------------------------------- ordering
+def score(D: np.ndarray, i: int, U: Sequence[int]) -> float:
+    """Eq. 3: M_i = sum_{j in U, j != i} f(T_{i<-j}, T_{j<-i}) with the
+    reading f(T_{i<-j}, T_{j<-i}) = min(0, T_{j<-i} - T_{i<-j})^2
+    = min(0, D[i, j])^2 (DirectLiNGAM's pairwise likelihood-ratio penalty: i
+    is penalised for every j that looks like its cause)."""
+    return float(sum(min(0.0, D[i, j]) ** 2 for j in U if j != i))
+
+
+def scores_over(D: np.ndarray, U: Sequence[int]) -> Dict[int, float]:
+    """Eq. 3 for every candidate i in U at once (the same sum as :func:`score`,
+    written as one array expression so that m = 400 runs in seconds)."""
+    Ua = np.asarray(list(U), dtype=np.int64)
+    sub = D[np.ix_(Ua, Ua)].copy()
+    np.fill_diagonal(sub, 0.0)  # j != i
+    vals = (np.minimum(0.0, sub) ** 2).sum(axis=1)
+    return {int(i): float(v) for i, v in zip(Ua, vals)}
+
+
+def order_heuristic(D: np.ndarray) -> Dict[str, object]:
+    """Algorithm 1: for k = 1..m pick c_k in U minimising M (Eq. 3) by lookups
+    in the static precomputed table, append it to K, remove it from U.  The
+    scores are recomputed from scratch over U at every step, as written.
+
+    Ties pick the lowest index.  Returns the order K and, per step, the sorted
+    candidate scores (for the relative-gap rule of :func:`order_gap_ok`).
+    """
+    D = np.asarray(D, dtype=np.float64)
+    m = D.shape[0]
+    U = list(range(m))
+    K: List[int] = []
+    steps = []
+    for _ in range(m):
+        scores = scores_over(D, U)
+        best = min(U, key=lambda i: (scores[i], i))
+        steps.append({"U": list(U), "scores": scores, "pick": best})
+        K.append(best)
+        U.remove(best)
+    return {"order": np.array(K, dtype=np.int64), "steps": steps}
+
+
+def order_standard(Xs: np.ndarray) -> Dict[str, object]:
+    """The iterative DirectLiNGAM search of Section 3 (steps 1-5): every
+    iteration re-standardizes the remaining variables, recomputes all pairwise
+    residuals and entropies, picks the minimiser of Eq. 3, then replaces every
+    remaining x_j by its residual on the pick (Eq. 4)."""
+    X = np.array(Xs, dtype=np.float64, copy=True)
+    m = X.shape[0]
+    U = list(range(m))
+    K: List[int] = []
+    steps = []
+    for _ in range(m):
+        if len(U) == 1:
+            K.append(U[0])
+            steps.append({"U": list(U), "scores": {U[0]: 0.0}, "pick": U[0]})
+            break
+        sub = standardize(X[U])
+        meas = pairwise_measure(sub)
+        Dsub = meas["D"]
+        loc = list(range(len(U)))
+        sub_scores = scores_over(Dsub, loc)
+        scores = {U[a]: sub_scores[a] for a in loc}
+        best = min(U, key=lambda i: (scores[i], i))
+        steps.append({"U": list(U), "scores": scores, "pick": best})
+        K.append(best)
+        U.remove(best)
+        for j in U:  # Eq. 4 on the data of this iteration
+            X[j] = residual(X[j], X[best])
+    return {"order": np.array(K, dtype=np.int64), "steps": steps}
+
+
+def relative_gap(scores: Dict[int, float]) -> float:
+    vals = sorted(scores.values())
+    if len(vals) < 2:
+        return math.inf
+    s1, s2 = vals[0], vals[1]
+    return (s2 - s1) / max(abs(s1), abs(s2), 1e-300)
+
+
+def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1e-6
+                 ) -> Tuple[bool, int, List[int]]:
+    """Order comparison rule: walk the candidate order step by step over ITS
+    OWN remaining set U; at each step the pick must be a minimiser of the
+    reference scores (Eq. 3 over D_ref), unless the reference scores of the
+    pick and the true minimiser lie within `rel_gap` relative of each other
+    (a near tie, where either choice is correct up to rounding).
+
+    Returns (ok, number of near-tie steps, list of failing steps)."""
+    D_ref = np.asarray(D_ref, dtype=np.float64)
+    m = D_ref.shape[0]
+    U = list(range(m))
+    ties = 0
+    bad: List[int] = []
+    if sorted(int(c) for c in order_gpu) != list(range(m)):
+        return False, 0, [-1]
+    for k, c in enumerate(order_gpu):
+        c = int(c)
+        scores = scores_over(D_ref, U)
+        smin = min(scores.values())
+        sc = scores[c]
+        if sc != smin:
+            denom = max(abs(sc), abs(smin), 1e-300)
+            if (sc - smin) / denom <= rel_gap:
+                ties += 1
+            else:
+                bad.append(k)
+        U.remove(c)
+    return (not bad), ties, bad
+
+
+# --------------------------------------------------------- B0 and B_tau
+def b0_ols(E: np.ndarray, order: Sequence[int]) -> np.ndarray:
+    """B0 from a causal order (Section 4: the instantaneous matrix of
+    VarLiNGAM).  Reading: row c_k of B0 holds the least-squares coefficients
+    of e_{c_k} on its predecessors e_{c_1..c_{k-1}} (with an intercept); the
+    first variable of the order has no parents.  B0[i, j] is the effect j -> i.
+    """
+    E = np.asarray(E, dtype=np.float64)
+    m, n = E.shape
+    B0 = np.zeros((m, m))
+    order = [int(c) for c in order]
+    for k in range(1, m):
+        tgt = order[k]
+        preds = order[:k]
+        A = np.hstack([E[preds].T, np.ones((n, 1))])
+        coef, *_ = np.linalg.lstsq(A, E[tgt], rcond=None)
+        B0[tgt, preds] = coef[:-1]
+    return B0
+
+
+def b0_ldl(E: np.ndarray, order: Sequence[int]) -> np.ndarray:
+    """Second, independent route to the same B0: with the centred covariance
+    S of E permuted into the causal order, S_perm = L diag(d) L^T with L unit
+    lower triangular, and I - L^{-1} holds every predecessor regression at
+    once (sequential regression = Cholesky)."""
+    E = np.asarray(E, dtype=np.float64)
+    m, n = E.shape
+    order = np.asarray(order, dtype=np.int64)
+    C = E - E.mean(axis=1, keepdims=True)
+    S = C @ C.T / n
+    Sp = S[np.ix_(order, order)]
+    Lc = scipy.linalg.cholesky(Sp, lower=True)
+    L = Lc / np.diag(Lc)[None, :]
+    Linv = scipy.linalg.solve_triangular(L, np.eye(m), lower=True, unit_diagonal=True)
+    Bp = np.eye(m) - Linv
+    B0 = np.zeros((m, m))
+    B0[np.ix_(order, order)] = Bp
+    return B0
+
+
+def btau(B0: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """Lagged effects of the structural VAR: x_t = B0 x_t + sum B_tau x_{t-tau}
+    + e_t has reduced form M_tau = (I - B0)^{-1} B_tau, so
+    B_tau = (I - B0) M_tau (VarLiNGAM, Hyvarinen et al. 2010)."""
+    m = B0.shape[0]
+    return np.stack([(np.eye(m) - B0) @ M[t] for t in range(M.shape[0])])
+
+
+# ------------------------------------------------------------ pipeline
+def varlingam(X: np.ndarray, p: int, method: str = "heuristic") -> Dict[str, object]:
+    """Whole method on one series.  'heuristic' = the paper's Algorithm 1 on
+    the VAR residuals (the data are never refined); 'standard' = iterative
+    DirectLiNGAM (Section 3).  B0 by predecessor OLS, B_tau = (I - B0) M."""
+    M, E = var_ols(X, p)
+    Xs = standardize(E)
+    out: Dict[str, object] = {"M": M, "E": E}
+    if method == "heuristic":
+        meas = pairwise_measure(Xs)
+        out.update(meas)
+        od = order_heuristic(meas["D"])
+    elif method == "standard":
+        od = order_standard(Xs)
+    else:
+        raise ValueError(method)
+    out["order"] = od["order"]
+    out["steps"] = od["steps"]
+    B0 = b0_ols(E, od["order"])
+    out["B0"] = B0
+    out["Btau"] = btau(B0, M)
+    return out
