@@ -1,0 +1,176 @@
+/*
+ * varlingam_gb300.h -- C ABI of the GB300 (sm_103a) approximate-ordering
+ * VarLiNGAM library (Jiao, Guo, Luk: "Scalable Time-Series Causal Discovery
+ * with Approximate Causal Ordering").
+ *
+ * The method (one series):
+ *   1. fit a VAR(p) by least squares and keep its residuals E     (Sec. 4.1)
+ *   2. precompute, once, the variable entropies E_x and the entropies E_r of
+ *      all m(m-1) standardized pairwise regression residuals, giving the
+ *      m x m likelihood-ratio matrix D                   (Sec. 4.2, Eqs. 1-2)
+ *   3. order the variables by m greedy argmins of Eq. 3 over that static
+ *      matrix                                                  (Algorithm 1)
+ *   4. estimate B0 from the order and B_tau = (I - B0) M_tau       (Sec. 4)
+ *
+ * Conventions shared by every call:
+ *   - All array arguments are DEVICE pointers owned by the caller; the library
+ *     never frees or retains them after the call returns.  Matrices are dense,
+ *     row-major, FP64 unless stated.
+ *   - Calls are asynchronous on the handle's CUDA stream.  Errors detectable on
+ *     the host (NULL pointers, bad sizes) return at once and launch nothing.
+ *     Errors found on the device (non-finite data, zero variance, a singular
+ *     system) are recorded in a sticky status word and returned by vl_sync().
+ *   - Outputs are undefined when a call returns an error or when vl_sync()
+ *     reports one.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - vl_precision selects the internal arithmetic; user-visible arrays are
+ *     FP64 either way.  VL_PREC_MIXED runs the O(m^2 n) and O(m^3) work in
+ *     FP32 with compensated FP32 sums and FP64 cross-block reductions;
+ *     VL_PREC_FP64 runs every step in FP64 (the plain comparison path).
+ *   - The handle grows its device workspace on demand (cudaMalloc).  Call
+ *     vl_reserve() first to make later calls allocation-free.
+ */
+#ifndef VARLINGAM_GB300_H
+#define VARLINGAM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vl_handle_s* vl_handle;
+
+typedef enum {
+  VL_OK = 0,
+  VL_ERR_ARG = 1,         /* NULL pointer or invalid enum                        */
+  VL_ERR_SHAPE = 2,       /* sizes out of range (m < 2, p < 1, ld too small ...) */
+  VL_ERR_RANK = 3,        /* VAR or B0 normal equations not positive definite,
+                             or n - p <= m p + 1 (no unique VAR fit)            */
+  VL_ERR_DEGENERATE = 4,  /* a zero-variance variable or a pair with
+                             1 - rho^2 < 1e-12 (residual identically zero)      */
+  VL_ERR_NONFINITE = 5,   /* NaN or Inf in the input                            */
+  VL_ERR_CUDA = 6,        /* a CUDA runtime call failed                         */
+  VL_ERR_NOMEM = 7,       /* workspace allocation failed                        */
+  VL_ERR_TIMEOUT = 8,     /* a bounded device wait gave up                      */
+  VL_ERR_UNSUPPORTED = 9  /* size beyond this build's limits                    */
+} vl_status;
+
+typedef enum { VL_PREC_FP64 = 0, VL_PREC_MIXED = 1 } vl_precision;
+
+/* Largest m any call accepts (the ordering kernel keeps m scores per CTA). */
+#define VL_MAX_M 4096
+
+/* Create a handle on CUDA device `device` that issues its work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * workspace_bytes > 0 preallocates that much device workspace.
+ * Returns VL_ERR_CUDA if the device cannot be selected. */
+vl_status vl_create(vl_handle* out, int device, void* cuda_stream, size_t workspace_bytes);
+
+/* Release the handle and its workspace (synchronises its stream first). */
+vl_status vl_destroy(vl_handle h);
+
+/* Change the stream subsequent calls are issued on. */
+vl_status vl_set_stream(vl_handle h, void* cuda_stream);
+
+/* Grow the workspace so that every single-series call on sizes up to
+ * (m, n, p) runs without allocating. */
+vl_status vl_reserve(vl_handle h, int m, int n, int p);
+
+/* Wait for the stream, then return and clear the first device-side error
+ * recorded since the last vl_sync (VL_OK if none). */
+vl_status vl_sync(vl_handle h);
+
+/* Diagnostics.  vl_profile_events: when both are non-NULL, later calls
+ * record start_event / stop_event (cudaEvent_t) on the handle's stream
+ * immediately before and after the pairwise-moment kernel, so a caller can
+ * time that kernel alone; NULL, NULL turns it off.  vl_kernel_launches:
+ * number of CUDA kernels this library has launched in the process. */
+vl_status vl_profile_events(vl_handle h, void* start_event, void* stop_event);
+unsigned long long vl_kernel_launches(void);
+
+/* Human-readable text of the last error on this handle (never NULL). */
+const char* vl_last_error(vl_handle h);
+
+/*
+ * VAR(p) least-squares fit with intercept (Sec. 4.1; Sec. 2.1: VarLiNGAM
+ * fits a VAR first and passes its residuals on):
+ *     x_t = c + sum_{tau=1..p} M_tau x_{t-tau} + e_t ,   t = p .. n-1.
+ * X   : m x n, row i = variable i over time, row stride ldx >= n (elements).
+ * M   : output, p*m*m, M[(tau-1)*m*m + i*m + k] = effect of x_k(t-tau) on x_i(t).
+ * E   : output, m x (n-p) residuals, row stride n-p.  May be NULL.
+ * Requires m >= 2, p >= 1, n - p > m p + 1 (else VL_ERR_RANK).
+ */
+vl_status vl_var_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, int p,
+                     vl_precision prec, double* M, double* E);
+
+/*
+ * One-time pairwise precomputation (Sec. 4.2 items 1-2; Algorithm 1, the two
+ * precompute calls; Eqs. 1-2 of Sec. 3).  Each row of E is standardized
+ * (population variance).  For every ordered pair (i, j), i != j, the residual
+ * r_{i<-j} = x_i - rho_ij x_j (Eq. 1) is rescaled to unit variance and its
+ * entropy approximated by
+ *     H(u) = (1 + log 2 pi)/2 - k1 (E log cosh u - gamma)^2 - k2 (E u e^{-u^2/2})^2
+ * with k1 = 79.047, k2 = 7.4129, gamma = 0.37457.
+ * E   : m x n_eff, row stride lde >= n_eff.
+ * Hx  : output m,   Hx[i] = H(x_i)                       (may be NULL)
+ * Hr  : output m*m, Hr[i*m+j] = H(r_{i<-j}), diagonal 0  (may be NULL)
+ * D   : output m*m, D[i*m+j] = Hx[j] + Hr[i*m+j] - Hx[i] - Hr[j*m+i]
+ *       (= T_{j<-i} - T_{i<-j}; > 0 favours i -> j; antisymmetric).
+ * Requires m >= 2, n_eff >= 2.
+ */
+vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
+                              vl_precision prec, double* Hx, double* Hr, double* D);
+
+/*
+ * Algorithm 1 over the static matrix D: for k = 1..m pick
+ *     c_k = argmin_{i in U} sum_{j in U, j != i} min(0, D[i*m+j])^2      (Eq. 3)
+ * (ties -> lowest index), append it, remove it from U.
+ * order : output m int32 (causes first).
+ * gap   : output m doubles or NULL; gap[k] = (S_2nd - S_min) / max(|S_min|,
+ *         |S_2nd|, 1e-300) at step k (+inf when one candidate is left).
+ */
+vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, double* gap);
+
+/*
+ * B0 and B_tau from a causal order (Sec. 4: the instantaneous matrix of
+ * VarLiNGAM): row order[k] of B0 holds the least-squares coefficients of
+ * e_{order[k]} on e_{order[0..k-1]}; then B_tau = (I - B0) M_tau.
+ * E     : m x n_eff residuals, row stride lde.   order : m int32 (device).
+ * M     : p*m*m as produced by vl_var_fit.
+ * B0    : output m*m, B0[i*m+j] = effect of j on i.
+ * Btau  : output p*m*m (may be NULL when p == 0 or not wanted).
+ */
+vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
+                   const int32_t* order, const double* M, int p,
+                   double* B0, double* Btau);
+
+/* One series for the batched call.  Device pointers; D may be NULL. */
+typedef struct {
+  const double* X;  /* m x n, row stride ldx                 */
+  int64_t ldx;
+  int m, n, p;
+  int32_t* order;   /* out: m                                 */
+  double* B0;       /* out: m*m                               */
+  double* Btau;     /* out: p*m*m                             */
+  double* M;        /* out: p*m*m                             */
+  double* D;        /* out: m*m or NULL                       */
+} vl_instance;
+
+/*
+ * The whole method (steps 1-4 above) for `count` independent series of
+ * possibly different (m, n, p), issued as one sequence of batched kernels on
+ * the handle's stream.  inst and inst_status are HOST arrays of length
+ * count; inst_status[k] receives the instance's own status after the call
+ * has completed (the call synchronises the stream).  Returns the first
+ * non-OK instance status, or a host-side error.
+ */
+vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_precision prec,
+                         vl_status* inst_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VARLINGAM_GB300_H */

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (written here, used everywhere below):
+  D            max |D_gpu - D_ref| <= 1e-5 * max |D_ref|
+  Hx, Hr       |dH| <= 1e-5 * max(|H_ref|, H_nu), H_nu = 1.4189 the entropy of
+               N(0,1): relative where H is O(1), and relative to the entropy
+               scale where a heavy-tailed variable drives H towards zero
+  order        identical wherever the oracle's relative score gap > 1e-6
+  B0, B_tau    1e-4 absolute (B0 from the GPU's order, compared with the
+               oracle's predecessor regression on that same order)
+  M            1e-5 absolute (mixed) / 1e-9 (FP64)
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+D_REL = 1e-5
+H_REL = 1e-5
+GAP = 1e-6
+B_ABS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def h(vl):
+    handle = vl.Handle(0)
+    yield handle
+    handle.close()
+
+
+_ref_cache = {}
+
+
+def _oracle_measure(key, E):
+    if key not in _ref_cache:
+        _ref_cache[key] = oracle.pairwise_measure(oracle.standardize(E))
+    return _ref_cache[key]
+
+
+def _measure_gpu(vl, h, E, prec):
+    m, n = E.shape
+    Et = torch.from_numpy(np.ascontiguousarray(E)).cuda()
+    f64 = dict(dtype=torch.float64, device="cuda")
+    Hx = torch.empty(m, **f64)
+    Hr = torch.empty((m, m), **f64)
+    D = torch.empty((m, m), **f64)
+    vl.vl_pairwise_measure(h, Et, prec, Hx, Hr, D)
+    h.sync()
+    return Hx.cpu().numpy(), Hr.cpu().numpy(), D.cpu().numpy()
+
+
+def _check_measure(ref, Hx, Hr, D):
+    dmax = np.abs(ref["D"]).max()
+    assert np.abs(D - ref["D"]).max() <= D_REL * dmax, np.abs(D - ref["D"]).max() / dmax
+    assert np.allclose(D, -D.T, atol=1e-15 + 1e-12 * dmax)
+    scale_x = np.maximum(np.abs(ref["Ex"]), oracle.H_GAUSS)
+    assert np.max(np.abs(Hx - ref["Ex"]) / scale_x) <= H_REL
+    off = ~np.eye(D.shape[0], dtype=bool)
+    scale_r = np.maximum(np.abs(ref["Er"]), oracle.H_GAUSS)
+    assert np.max((np.abs(Hr - ref["Er"]) / scale_r)[off]) <= H_REL
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("m,n,seed", [(2, 257, 1), (3, 1001, 2), (10, 503, 3), (37, 777, 4),
+                                      (33, 64, 5), (64, 2049, 6)])
+def test_pairwise_measure_small(vl, h, prec, m, n, seed):
+    """Several tiles (m > 32), ragged tails (n not a multiple of the stage or
+    of the 8-sample run), a single pair (m = 2)."""
+    rng = np.random.default_rng(seed)
+    E = rng.laplace(size=(m, n))
+    E[1:] += 0.5 * E[:-1]
+    ref = _oracle_measure(("small", m, n, seed), E)
+    Hx, Hr, D = _measure_gpu(vl, h, E, prec)
+    _check_measure(ref, Hx, Hr, D)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_causal_order_matches_algorithm1(vl, h, prec):
+    rng = np.random.default_rng(11)
+    for m in (2, 5, 31, 97):
+        A = rng.normal(size=(m, m))
+        D = A - A.T
+        Dt = torch.from_numpy(D).cuda()
+        order = torch.empty(m, dtype=torch.int32, device="cuda")
+        gap = torch.empty(m, dtype=torch.float64, device="cuda")
+        vl.vl_causal_order(h, Dt, order, gap)
+        h.sync()
+        ref = oracle.order_heuristic(D)
+        assert list(order.cpu().numpy()) == [int(c) for c in ref["order"]]
+        g = gap.cpu().numpy()
+        for k, stp in enumerate(ref["steps"]):
+            rg = oracle.relative_gap(stp["scores"])
+            if math.isinf(rg):
+                assert math.isinf(g[k])
+            else:
+                assert abs(g[k] - rg) <= 1e-9 * max(1.0, abs(rg))
+
+
+def test_causal_order_ties_lowest_index(vl, h):
+    D = torch.zeros((6, 6), dtype=torch.float64, device="cuda")
+    order = torch.empty(6, dtype=torch.int32, device="cuda")
+    vl.vl_causal_order(h, D, order)
+    h.sync()
+    assert list(order.cpu().numpy()) == [0, 1, 2, 3, 4, 5]
+
+
+def _fit_steps(vl, h, inst, prec):
+    X = torch.from_numpy(inst.X).cuda()
+    return vl.fit(h, X, inst.p, prec=prec, steps=True)
+
+
+def _ref_pipeline(key, inst):
+    if key not in _ref_cache:
+        M, E = oracle.var_ols(inst.X, inst.p)
+        meas = oracle.pairwise_measure(oracle.standardize(E))
+        od = oracle.order_heuristic(meas["D"])
+        _ref_cache[key] = dict(M=M, E=E, order=od["order"], **meas)
+    return _ref_cache[key]
+
+
+def _check_pipeline(ref, out, prec, p):
+    M = out["M"].cpu().numpy()
+    assert np.abs(M - ref["M"]).max() <= (1e-5 if prec == "mixed" else 1e-9)
+    E = out["E"].cpu().numpy()
+    assert np.abs(E - ref["E"]).max() <= (1e-5 if prec == "mixed" else 1e-9) * np.abs(ref["E"]).max()
+    _check_measure(ref, out["Hx"].cpu().numpy(), out["Hr"].cpu().numpy(), out["D"].cpu().numpy())
+    order = out["order"].cpu().numpy()
+    ok, ties, bad = oracle.order_gap_ok(order, ref["D"], GAP)
+    assert ok, f"order differs beyond the near-tie rule at steps {bad}"
+    B0_ref = oracle.b0_ols(ref["E"], order)
+    assert np.abs(out["B0"].cpu().numpy() - B0_ref).max() <= B_ABS
+    Bt_ref = oracle.btau(B0_ref, ref["M"])
+    assert np.abs(out["Btau"].cpu().numpy() - Bt_ref).max() <= B_ABS
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("name", ["pr1", "fmri"])
+def test_pipeline_small_workloads(vl, h, prec, name):
+    inst = synth.make_config(name)
+    ref = _ref_pipeline(name, inst)
+    out = _fit_steps(vl, h, inst, prec)
+    _check_pipeline(ref, out, prec, inst.p)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_pipeline_server_workload(vl, h, prec):
+    inst = synth.make_config("server")  # m=120, n=10000, p=3
+    ref = _ref_pipeline("server", inst)
+    out = _fit_steps(vl, h, inst, prec)
+    _check_pipeline(ref, out, prec, inst.p)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_pipeline_finance_workload(vl, h, prec):
+    inst = synth.make_config("finance")  # m=400, n=2500, p=1
+    ref = _ref_pipeline("finance", inst)
+    out = _fit_steps(vl, h, inst, prec)
+    _check_pipeline(ref, out, prec, inst.p)
+
+
+def test_batched_single_matches_steps(vl, h):
+    inst = synth.make_config("pr1")
+    X = torch.from_numpy(inst.X).cuda()
+    a = vl.fit(h, X, inst.p, prec="mixed", steps=False)
+    b = vl.fit(h, X, inst.p, prec="mixed", steps=True)
+    assert torch.equal(a["order"], b["order"])
+    assert (a["D"] - b["D"]).abs().max().item() <= 1e-12
+    assert (a["B0"] - b["B0"]).abs().max().item() <= 1e-5
+
+
+# ------------------------------------------------------------ errors
+def test_errors_reported(vl, h):
+    f64 = dict(dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(0)
+    # zero-variance variable -> VL_ERR_DEGENERATE at sync
+    E = rng.normal(size=(4, 300))
+    E[2] = 3.0
+    Et = torch.from_numpy(E).cuda()
+    D = torch.empty((4, 4), **f64)
+    vl.vl_pairwise_measure(h, Et, "mixed", None, None, D)
+    with pytest.raises(vl.VLError) as ei:
+        h.sync()
+    assert ei.value.code == 4
+    # exactly collinear pair -> degenerate
+    E = rng.normal(size=(3, 300))
+    E[1] = -2.0 * E[0] + 1.0
+    vl.vl_pairwise_measure(h, torch.from_numpy(E).cuda(), "mixed", None, None,
+                           torch.empty((3, 3), **f64))
+    with pytest.raises(vl.VLError) as ei:
+        h.sync()
+    assert ei.value.code == 4
+    # NaN -> VL_ERR_NONFINITE
+    E = rng.normal(size=(3, 300))
+    E[0, 17] = np.nan
+    vl.vl_pairwise_measure(h, torch.from_numpy(E).cuda(), "fp64", None, None,
+                           torch.empty((3, 3), **f64))
+    with pytest.raises(vl.VLError) as ei:
+        h.sync()
+    assert ei.value.code == 5
+    # rank-deficient VAR caught on the host
+    X = torch.from_numpy(rng.normal(size=(5, 7))).cuda()  # n - p = 6 <= m p + 1
+    with pytest.raises(vl.VLError) as ei:
+        vl.vl_var_fit(h, X, 1, "mixed", torch.empty((1, 5, 5), **f64), None)
+    assert ei.value.code == 3
+    # a collinear series makes the VAR normal equations singular -> RANK
+    Xn = rng.normal(size=(4, 400))
+    Xn[3] = Xn[1]
+    vl.vl_var_fit(h, torch.from_numpy(Xn).cuda(), 1, "fp64", torch.empty((1, 4, 4), **f64), None)
+    with pytest.raises(vl.VLError) as ei:
+        h.sync()
+    assert ei.value.code == 3
+    h.sync()  # status was cleared
+
+
+def test_bad_arguments(vl, h):
+    f64 = dict(dtype=torch.float64, device="cuda")
+    E = torch.zeros((1, 100), **f64)
+    with pytest.raises(vl.VLError) as ei:
+        vl.vl_pairwise_measure(h, E, "mixed", None, None, torch.empty((1, 1), **f64))
+    assert ei.value.code == 2
+    lib = vl.lib()
+    assert lib.vl_causal_order(h.h, None, 4, None, None) == 1
+    assert lib.vl_pairwise_measure(h.h, None, 10, 4, 10, 1, None, None, None) == 1
