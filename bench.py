@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the approximate-ordering VarLiNGAM hot path on GB300.
+
+One step = the whole method on one series already resident in HBM:
+VAR(p) fit -> pairwise measure (the O(m^2 n) precomputation) -> Algorithm 1
+ordering -> B0 and B_tau.  Default workload: the finance-shaped series,
+m = 400 variables, n = 2500 samples, p = 1, Student-t3 shocks.
+
+Prints ONE JSON line (rank 0).  `value` = pair-samples per step / device time
+per step, pair-samples = m (m - 1) / 2 * (n - p).  The L2 cache is flushed
+(256 MiB write) before every timed step; only the step is inside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (the plain restatement of the
+paper) on a bounded sample of the same workload, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-samples/s of pairwise measure; end-to-end ms at m=400 (mixed vs FP64)"
+UNIT = "pair-samples/s"
+ALG_OPS_PER_PAIR_SAMPLE = 18  # see the design doc: 2 x (2 form w, 2 ex2, 1 prod, 1 |w|, 2 exp arg, 1 acc)
+SM_LANES_PER_CLK = 128  # FP32/issue lanes per SM per clock (4 SMSPs x 32)
+MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="finance", choices=["pr1", "fmri", "server", "finance"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_desc(inst, name):
+    return {"pr1": "pr1: m=10 n=1000 p=1 uniform shocks",
+            "fmri": "fmri-like: m=50 n=200 p=1 |g|^1.5 shocks",
+            "server": "server-monitoring-like: m=120 n=10000 p=3 Laplace shocks",
+            "finance": "finance-like: m=400 n=2500 p=1 Student-t3 shocks"}[name]
+
+
+def pair_samples(m, n, p):
+    return m * (m - 1) // 2 * (n - p)
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample_run(inst, m_s):
+    import oracle
+
+    X = inst.X[:m_s]
+    t0 = time.perf_counter()
+    oracle.varlingam(X, inst.p)
+    return time.perf_counter() - t0
+
+
+def cpu_sample_size(inst, seconds):
+    """Largest leading-variable sample whose oracle run takes about `seconds`."""
+    m_s = 12
+    dt = oracle_sample_run(inst, m_s)
+    # cost ~ m^2 n: scale up to the target
+    target = int(m_s * math.sqrt(max(seconds, 0.5) / max(dt, 1e-3)))
+    m_s = max(4, min(inst.m, target))
+    return m_s
+
+
+def cpu_baseline(inst, seconds):
+    m_s = cpu_sample_size(inst, seconds)
+    dt = oracle_sample_run(inst, m_s)
+    val = pair_samples(m_s, inst.n, inst.p) / dt
+    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"whole FP64 oracle (VAR, pairwise measure, Algorithm 1, B0) on the first "
+                      f"{m_s} of {inst.m} variables, n={inst.n}, p={inst.p}: {dt:.1f} s, "
+                      f"single-threaded NumPy"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, dev):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{dev}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2409_05500_gb300 as vl
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    inst = synth.make_config(args.workload)
+    m, n, p = inst.m, inst.n, inst.p
+    n_eff = n - p
+    PS = pair_samples(m, n, p)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    h = vl.Handle(dev, stream)
+    f64 = dict(dtype=torch.float64, device=f"cuda:{dev}")
+    X = torch.from_numpy(inst.X).to(f"cuda:{dev}")
+    out = vl.alloc_outputs(m, p, dev)
+    E = torch.empty((m, n_eff), **f64)
+    Hx = torch.empty(m, **f64)
+    Hr = torch.empty((m, m), **f64)
+    gap = torch.empty(m, **f64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def step(prec, Xd):
+        vl.vl_var_fit(h, Xd, p, prec, out["M"], E)
+        vl.vl_pairwise_measure(h, E, prec, Hx, Hr, out["D"])
+        vl.vl_causal_order(h, out["D"], out["order"], gap)
+        vl.vl_fit_b(h, E, out["order"], out["M"], prec, out["B0"], out["Btau"])
+
+    def timed(prec, K, W, kernel_events=False):
+        for _ in range(W):
+            step(prec, X)
+        h.sync()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        l0 = vl.kernel_launches()
+        for k in range(K):
+            flush.zero_()
+            if kernel_events:
+                # torch only times events it has recorded once; the library
+                # then re-records both around the pairwise kernel
+                kev[k][0].record(stream)
+                kev[k][1].record(stream)
+                h.profile_events(*kev[k])
+            ev[k][0].record(stream)
+            step(prec, X)
+            ev[k][1].record(stream)
+        h.sync()
+        torch.cuda.synchronize()
+        launches = vl.kernel_launches() - l0
+        h.profile_events(None, None)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        kms = [a.elapsed_time(b) for a, b in kev] if kernel_events else None
+        return ms, kms, launches
+
+    # warm-up, then the timed region with clocks sampled during it
+    clocks = ClockSampler(dev)
+    ms, kms, launches = timed(args.prec, args.steps, args.warmup, kernel_events=True)
+    clk = clocks.stop()
+    tot_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * PS / (ms_per_step * 1e-3)
+
+    # FP64 GPU comparison path (same steps, every kernel in FP64)
+    fp64_ms = None
+    if not args.no_fp64_compare and args.prec == "mixed":
+        ms64, _, _ = timed("fp64", max(3, min(5, args.steps)), 1)
+        fp64_ms = sum(ms64) / len(ms64)
+
+    # end to end through the C ABI with host buffers: pinned X in, order,
+    # B0, B_tau out, copies inside the events
+    Xh = torch.from_numpy(inst.X).pin_memory()
+    outs_h = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory()
+              for k in ("order", "B0", "Btau")}
+    Xd = torch.empty_like(X)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Xd.copy_(Xh, non_blocking=True)
+        step(args.prec, Xd)
+        for key, t in outs_h.items():
+            t.copy_(out[key], non_blocking=True)
+        b.record(stream)
+        h.sync()
+        stream.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
+
+    # roofline of the dominant kernel (pairwise moments), live CUDA events
+    k_ms = statistics.mean(kms) if kms else None
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak = sms * SM_LANES_PER_CLK * MAX_SM_MHZ * 1e6 / 1e12  # Tops/s at max clock
+    roof = None
+    if k_ms:
+        ach = PS * ALG_OPS_PER_PAIR_SAMPLE / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
+                "unit": "Tops/s", "frac": round(ach / peak, 4), "traffic": None,
+                "kernel": "pairwise_f32_kernel" if args.prec == "mixed" else "pairwise_f64_kernel",
+                "kernel_ms": round(k_ms, 4),
+                "kernel_pair_samples_per_s": PS / (k_ms * 1e-3),
+                "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} lanes/clk x {MAX_SM_MHZ:.0f} MHz; "
+                              f"{ALG_OPS_PER_PAIR_SAMPLE} algorithmic ops per pair-sample"}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(inst, args.workload), "m": m, "n": n, "p": p,
+                   "precision": args.prec, "pair_samples_per_step": PS,
+                   "l2": "flushed by a 256 MiB write before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fp64_ms_per_step": fp64_ms,
+        "e2e": {"value": world * PS / (e2e_step * 1e-3), "unit": UNIT, "ms_per_step": e2e_step,
+                "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+    h.close()
+    return res
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: each step is the whole method on the first m_s variables."""
+    import synth
+
+    inst = synth.make_config(args.workload)
+    per_step = max(0.5, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    m_s = cpu_sample_size(inst, per_step)
+    for _ in range(args.warmup):
+        oracle_sample_run(inst, m_s)
+    dts = [oracle_sample_run(inst, m_s) for _ in range(args.steps)]
+    dt = sum(dts) / len(dts)
+    val = pair_samples(m_s, inst.n, inst.p) / dt
+    sample = (f"whole FP64 oracle on the first {m_s} of {inst.m} variables, n={inst.n}, "
+              f"p={inst.p}, single-threaded NumPy")
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(inst, args.workload), "m": inst.m, "n": inst.n,
+                       "p": inst.p, "sample_m": m_s},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

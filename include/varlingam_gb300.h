@@ -138,12 +138,14 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
  * VarLiNGAM): row order[k] of B0 holds the least-squares coefficients of
  * e_{order[k]} on e_{order[0..k-1]}; then B_tau = (I - B0) M_tau.
  * E     : m x n_eff residuals, row stride lde.   order : m int32 (device).
- * M     : p*m*m as produced by vl_var_fit.
+ * M     : p*m*m as produced by vl_var_fit (may be NULL when Btau is NULL).
+ * prec  : VL_PREC_MIXED factors the permuted covariance in FP32 (B0 error
+ *         ~1e-6 for well-conditioned residuals), VL_PREC_FP64 in FP64.
  * B0    : output m*m, B0[i*m+j] = effect of j on i.
  * Btau  : output p*m*m (may be NULL when p == 0 or not wanted).
  */
 vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
-                   const int32_t* order, const double* M, int p,
+                   const int32_t* order, const double* M, int p, vl_precision prec,
                    double* B0, double* Btau);
 
 /* One series for the batched call.  Device pointers; D may be NULL. */

@@ -67,7 +67,7 @@ def _load() -> ctypes.CDLL:
         "vl_var_fit": [P, P, I64, I, I, I, I, P, P],
         "vl_pairwise_measure": [P, P, I64, I, I, I, P, P, P],
         "vl_causal_order": [P, P, I, P, P],
-        "vl_fit_b": [P, P, I64, I, I, P, P, I, P, P],
+        "vl_fit_b": [P, P, I64, I, I, P, P, I, I, P, P],
         "vl_fit_batched": [P, ctypes.POINTER(vl_instance), I, I, ctypes.POINTER(I)],
         "vl_profile_events": [P, P, P],
     }
@@ -172,11 +172,11 @@ def vl_causal_order(h: Handle, D: torch.Tensor, order: torch.Tensor,
 
 
 def vl_fit_b(h: Handle, E: torch.Tensor, order: torch.Tensor, M: Optional[torch.Tensor],
-             B0: torch.Tensor, Btau: Optional[torch.Tensor]) -> None:
+             prec: str, B0: torch.Tensor, Btau: Optional[torch.Tensor]) -> None:
     m, n_eff = E.shape
     p = 0 if M is None else M.shape[0]
-    h.check(_lib.vl_fit_b(h.h, _ptr(E), E.stride(0), m, n_eff, _ptr(order), _ptr(M), p, _ptr(B0),
-                          _ptr(Btau)), "vl_fit_b")
+    h.check(_lib.vl_fit_b(h.h, _ptr(E), E.stride(0), m, n_eff, _ptr(order), _ptr(M), p,
+                          PRECISIONS[prec], _ptr(B0), _ptr(Btau)), "vl_fit_b")
 
 
 def vl_fit_batched(h: Handle, instances: Sequence[Dict[str, torch.Tensor]], prec: str):
@@ -223,6 +223,6 @@ def fit(h: Handle, X: torch.Tensor, p: int, prec: str = "mixed", steps: bool = F
     vl_var_fit(h, X, p, prec, out["M"], E)
     vl_pairwise_measure(h, E, prec, out["Hx"], out["Hr"], out["D"])
     vl_causal_order(h, out["D"], out["order"], out["gap"])
-    vl_fit_b(h, E, out["order"], out["M"], out["B0"], out["Btau"])
+    vl_fit_b(h, E, out["order"], out["M"], prec, out["B0"], out["Btau"])
     h.sync()
     return out

@@ -432,16 +432,18 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
 }
 
 vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
-                   const int32_t* order, const double* M, int p, double* B0, double* Btau) {
+                   const int32_t* order, const double* M, int p, vl_precision prec, double* B0,
+                   double* Btau) {
   if (!h) return VL_ERR_ARG;
   if (!E || !order || !B0) return fail(h, VL_ERR_ARG, "vl_fit_b: E, order and B0 must not be NULL");
   if (p > 0 && Btau && !M) return fail(h, VL_ERR_ARG, "vl_fit_b: Btau requested without M");
   if (m < 2 || n_eff < 2 || p < 0 || m > VL_MAX_M || lde < n_eff)
     return fail(h, VL_ERR_SHAPE, "vl_fit_b: bad sizes");
+  if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
   DeviceGuard g(h->device);
-  // vl_fit_b takes no precision argument and runs in FP64; vl_fit_batched
-  // with VL_PREC_MIXED runs the same steps in FP32.
-  return fit_b_impl<double>(h, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr);
+  return prec == VL_PREC_MIXED
+             ? fit_b_impl<float>(h, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr)
+             : fit_b_impl<double>(h, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr);
 }
 
 vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_precision prec,
