@@ -163,15 +163,26 @@ def run_ours(args, rank, world):
     gap = torch.empty(m, **f64)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
 
-    def step(prec, Xd):
+    def step(prec, Xd, marks=None):
+        def mark(i):
+            if marks is not None:
+                marks[i].record(stream)
+        mark(0)
         vl.vl_var_fit(h, Xd, p, prec, out["M"], E)
+        mark(1)
         vl.vl_pairwise_measure(h, E, prec, Hx, Hr, out["D"])
+        mark(2)
         vl.vl_causal_order(h, out["D"], out["order"], gap)
+        mark(3)
         vl.vl_fit_b(h, E, out["order"], out["M"], prec, out["B0"], out["Btau"])
+        mark(4)
+
+    def fused(prec, Xd):
+        vl.vl_fit(h, Xd, p, prec, out["M"], out["order"], out["B0"], out["Btau"], out["D"])
 
     def timed(prec, K, W, kernel_events=False):
         for _ in range(W):
-            step(prec, X)
+            fused(prec, X)
         h.sync()
         torch.cuda.synchronize()
         if world > 1:
@@ -190,7 +201,7 @@ def run_ours(args, rank, world):
                 kev[k][1].record(stream)
                 h.profile_events(*kev[k])
             ev[k][0].record(stream)
-            step(prec, X)
+            fused(prec, X)
             ev[k][1].record(stream)
         h.sync()
         torch.cuda.synchronize()
@@ -212,6 +223,15 @@ def run_ours(args, rank, world):
     ms_per_step = tot_ms / args.steps
     value = world * PS / (ms_per_step * 1e-3)
 
+    # per-phase split through the four separate calls (one extra step, outside
+    # the timed region; vl_fit_b recomputes the covariance there)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    flush.zero_()
+    step(args.prec, X, marks)
+    h.sync()
+    phases = {nm: round(marks[i].elapsed_time(marks[i + 1]), 4) for i, nm in
+              enumerate(["var_fit", "pairwise_measure", "causal_order", "fit_b"])}
+
     # FP64 GPU comparison path (same steps, every kernel in FP64)
     fp64_ms = None
     if not args.no_fp64_compare and args.prec == "mixed":
@@ -230,7 +250,7 @@ def run_ours(args, rank, world):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         Xd.copy_(Xh, non_blocking=True)
-        step(args.prec, Xd)
+        fused(args.prec, Xd)
         for key, t in outs_h.items():
             t.copy_(out[key], non_blocking=True)
         b.record(stream)
@@ -271,6 +291,7 @@ def run_ours(args, rank, world):
                    "l2": "flushed by a 256 MiB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "fp64_ms_per_step": fp64_ms,
+        "phase_ms": phases,
         "e2e": {"value": world * PS / (e2e_step * 1e-3), "unit": UNIT, "ms_per_step": e2e_step,
                 "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
                 "d2h_bytes_per_step": d2h},

@@ -148,6 +148,20 @@ vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
                    const int32_t* order, const double* M, int p, vl_precision prec,
                    double* B0, double* Btau);
 
+/*
+ * The whole method (steps 1-4 above) for one series, asynchronously on the
+ * handle's stream: VAR fit, pairwise measure, Algorithm 1, B0 and B_tau.  The
+ * residual covariance is computed once and shared by the measure and B0
+ * steps.  No host synchronisation; device errors surface at vl_sync().  After
+ * a first call has sized the workspace, later calls with the same or smaller
+ * sizes allocate nothing (they can then be captured in a CUDA graph).
+ * X : m x n (row stride ldx).  Outputs: M p*m*m, order m, B0 m*m, Btau p*m*m,
+ * D m*m (may be NULL).
+ */
+vl_status vl_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, int p,
+                 vl_precision prec, double* M, int32_t* order, double* B0, double* Btau,
+                 double* D);
+
 /* One series for the batched call.  Device pointers; D may be NULL. */
 typedef struct {
   const double* X;  /* m x n, row stride ldx                 */

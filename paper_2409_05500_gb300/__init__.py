@@ -34,7 +34,7 @@ VL_PREC_MIXED = 1
 PRECISIONS = {"fp64": VL_PREC_FP64, "mixed": VL_PREC_MIXED}
 
 EXPORTED = ("vl_create", "vl_destroy", "vl_set_stream", "vl_reserve", "vl_sync",
-            "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_var_fit",
+            "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_fit", "vl_var_fit",
             "vl_pairwise_measure", "vl_causal_order", "vl_fit_b", "vl_fit_batched")
 
 
@@ -69,6 +69,7 @@ def _load() -> ctypes.CDLL:
         "vl_causal_order": [P, P, I, P, P],
         "vl_fit_b": [P, P, I64, I, I, P, P, I, I, P, P],
         "vl_fit_batched": [P, ctypes.POINTER(vl_instance), I, I, ctypes.POINTER(I)],
+        "vl_fit": [P, P, I64, I, I, I, I, P, P, P, P, P],
         "vl_profile_events": [P, P, P],
     }
     for name, args in sig.items():
@@ -179,6 +180,14 @@ def vl_fit_b(h: Handle, E: torch.Tensor, order: torch.Tensor, M: Optional[torch.
                           PRECISIONS[prec], _ptr(B0), _ptr(Btau)), "vl_fit_b")
 
 
+def vl_fit(h: Handle, X: torch.Tensor, p: int, prec: str, M: torch.Tensor, order: torch.Tensor,
+           B0: torch.Tensor, Btau: torch.Tensor, D: Optional[torch.Tensor] = None) -> None:
+    """Whole method on one series, asynchronous on the handle's stream."""
+    m, n = X.shape
+    h.check(_lib.vl_fit(h.h, _ptr(X), X.stride(0), m, n, p, PRECISIONS[prec], _ptr(M),
+                        _ptr(order), _ptr(B0), _ptr(Btau), _ptr(D)), "vl_fit")
+
+
 def vl_fit_batched(h: Handle, instances: Sequence[Dict[str, torch.Tensor]], prec: str):
     """instances: dicts with X (m x n float64 CUDA), p, and output tensors
     order, B0, Btau, M and optionally D.  Returns the per-instance status
@@ -208,13 +217,12 @@ def alloc_outputs(m: int, p: int, device=None) -> Dict[str, torch.Tensor]:
 def fit(h: Handle, X: torch.Tensor, p: int, prec: str = "mixed", steps: bool = False):
     """Whole method on one series (device tensor X, m x n float64).  With
     steps=True the four calls run separately and E, Hx, Hr, D and the gaps
-    are returned too; otherwise vl_fit_batched with one instance."""
+    are returned too; otherwise the single fused call vl_fit."""
     m, n = X.shape
     out = alloc_outputs(m, p, X.device.index)
     if not steps:
-        st = vl_fit_batched(h, [dict(X=X, p=p, **out)], prec)
-        if st[0] != VL_OK:
-            raise VLError(st[0], _lib.vl_last_error(h.h).decode())
+        vl_fit(h, X, p, prec, out["M"], out["order"], out["B0"], out["Btau"], out["D"])
+        h.sync()
         return out
     f64 = dict(dtype=torch.float64, device=X.device)
     E = torch.empty((m, n - p), **f64)

@@ -65,30 +65,69 @@ struct DeviceGuard {
   }
 };
 
-// Carve a workspace layout twice: once to measure, once for real.
+// Where one step of the method runs: a stream, the status word its kernels
+// report to, and a device workspace it may overwrite.  Single calls use the
+// handle's own; a batch gives every stream of its pool one of these.
+struct Exec {
+  vl_handle h;
+  cudaStream_t s;
+  int* st;
+  void** ws;       // workspace pointer owned by the handle
+  size_t* ws_cap;  // and its capacity
+  bool measure;    // true: only accumulate the workspace size in `need`
+  size_t need;
+};
+
+Exec handle_exec(vl_handle h) {
+  return Exec{h, h->stream, h->status, &h->ws, &h->ws_cap, false, 0};
+}
+
+vl_status grow(vl_handle h, void** ws, size_t* cap, size_t bytes, cudaStream_t s) {
+  if (bytes <= *cap) return VL_OK;
+  if (*ws) {
+    cudaStreamSynchronize(s);
+    cudaFree(*ws);
+    *ws = nullptr;
+    *cap = 0;
+  }
+  size_t c = std::max(bytes, (size_t)8 << 20);
+  if (cudaMalloc(ws, c) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, VL_ERR_NOMEM, "workspace allocation of " + std::to_string(c) + " bytes failed");
+  }
+  *cap = c;
+  return VL_OK;
+}
+
+// Carve a workspace layout twice: once to measure, once for real.  In
+// measure mode only the size is recorded and the caller launches nothing.
 template <class F>
-vl_status with_workspace(vl_handle h, F&& carve) {
+vl_status with_workspace(Exec& x, F&& carve) {
   Arena probe;
   probe.base = nullptr;
   carve(probe);
-  vl_status s = ensure_ws(h, probe.off + 512);
+  if (x.measure) {
+    x.need = std::max(x.need, probe.off + 512);
+    return VL_OK;
+  }
+  vl_status s = grow(x.h, x.ws, x.ws_cap, probe.off + 512, x.s);
   if (s != VL_OK) return s;
   Arena a;
-  a.base = static_cast<char*>(h->ws);
-  a.cap = h->ws_cap;
+  a.base = static_cast<char*>(*x.ws);
+  a.cap = *x.ws_cap;
   carve(a);
   return VL_OK;
 }
 
-Ctx make_ctx(vl_handle h, double* part, size_t part_cap) {
-  return Ctx{h->stream, h->status, part, part_cap, h->num_sms};
+Ctx make_ctx(const Exec& x, double* part, size_t part_cap) {
+  return Ctx{x.s, x.st, part, part_cap, x.h->num_sms};
 }
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 // ------------------------------------------------------------- VAR fit
 template <class T>
-vl_status var_fit_impl(vl_handle h, const double* X, int64_t ldx, int m, int n, int p, double* M,
+vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int p, double* M,
                        double* E) {
   const int n_eff = n - p, mp = m * p, q = m * (p + 1);
   const int64_t ldc = round_up(n, 4);
@@ -96,7 +135,7 @@ vl_status var_fit_impl(vl_handle h, const double* X, int64_t ldx, int m, int n, 
   const size_t part_cap = (size_t)16 * std::max((size_t)m * m, (size_t)mp * mp);
   T *Xc, *Gzz, *Gzy, *dinv;
   double *mu, *wbar, *G, *cst, *Ew, *part, *diag0;
-  vl_status s = with_workspace(h, [&](Arena& a) {
+  vl_status s = with_workspace(x, [&](Arena& a) {
     Xc = a.take<T>((size_t)m * ldc);
     mu = a.take<double>(m);
     wbar = a.take<double>((size_t)(p + 1) * m);
@@ -109,11 +148,11 @@ vl_status var_fit_impl(vl_handle h, const double* X, int64_t ldx, int m, int n, 
     Ew = E ? nullptr : a.take<double>((size_t)m * n_eff);
     part = a.take<double>(part_cap);
   });
-  if (s != VL_OK) return s;
+  if (s != VL_OK || x.measure) return s;
   if (!E) E = Ew;
-  Ctx cx = make_ctx(h, part, part_cap);
-  cudaStream_t st = h->stream;
-  launch_var_prep<T>(X, ldx, m, n, p, Xc, ldc, mu, wbar, h->status, st);
+  Ctx cx = make_ctx(x, part, part_cap);
+  cudaStream_t st = x.s;
+  launch_var_prep<T>(X, ldx, m, n, p, Xc, ldc, mu, wbar, x.st, st);
   // lagged Gram: rows of Z (lags 1..p) against rows of W = [Y; Z]
   for (int t1 = 1; t1 <= p; ++t1)
     for (int b2 = 0; b2 <= p; ++b2) {
@@ -132,7 +171,7 @@ vl_status var_fit_impl(vl_handle h, const double* X, int64_t ldx, int m, int n, 
     View<T> B{Xc + (p - tau), 1, ldc};                 // B(t, k) = Xc[k][p - tau + t]
     launch_gemm<T, double>(cx, m, n_eff, m, -1.0, A, B, 1.0, E, n_eff, false);
   }
-  return check_launch(h, "vl_var_fit");
+  return check_launch(x.h, "vl_var_fit");
 }
 
 // ------------------------------------------------------- pairwise measure
@@ -144,10 +183,10 @@ struct CovOut {
 };
 
 template <class T>
-void cov_and_stats(vl_handle h, const Ctx& cx, const double* E, int64_t lde, int m, int n,
-                   const CovOut& o, void* scratch) {
-  cudaStream_t st = h->stream;
-  launch_standardize<T>(E, lde, m, n, o.mu, o.isd, o.hx, h->status, st);
+void cov_and_stats(const Ctx& cx, const double* E, int64_t lde, int m, int n, const CovOut& o,
+                   void* scratch) {
+  cudaStream_t st = cx.s;
+  launch_standardize<T>(E, lde, m, n, o.mu, o.isd, o.hx, cx.st, st);
   const int64_t ldc = round_up(n, 4);
   if constexpr (sizeof(T) == 4) {
     float* hi = static_cast<float*>(scratch);
@@ -170,19 +209,21 @@ size_t cov_scratch_bytes(int m, int n) {
 }
 
 template <class T>
-vl_status pairwise_impl(vl_handle h, const double* E, int64_t lde, int m, int n, double* Hx,
+vl_status pairwise_impl(Exec& x, const double* E, int64_t lde, int m, int n, double* Hx,
                         double* Hr, double* D, double* C_out) {
   const bool f32 = sizeof(T) == 4;
-  PairPlan pl = plan_pairwise(m, n, h->num_sms, !f32);
+  PairPlan pl = plan_pairwise(m, n, x.h->num_sms, !f32);
   const size_t part_cap = (size_t)16 * m * m;
-  const size_t nparts = (size_t)pl.splits * (f32 ? 3 : 2) * m * m;
+  // FP32 path: 6 floats (3 double-float sums) per residual per split;
+  // FP64 path: 2 doubles
+  const size_t nparts = (size_t)pl.splits * (f32 ? 3 : 2) * m * m;  // in 8-byte units
   CovOut o;
   void* scratch;
   float *rho32 = nullptr, *c32 = nullptr;
   double* rho64 = nullptr;
   T* xt;
   double *pparts, *gpart, *Hr_w, *D_w;
-  vl_status s = with_workspace(h, [&](Arena& a) {
+  vl_status s = with_workspace(x, [&](Arena& a) {
     o.C = C_out ? C_out : a.take<double>((size_t)m * m);
     o.mu = a.take<double>(m);
     o.isd = a.take<double>(m);
@@ -200,17 +241,18 @@ vl_status pairwise_impl(vl_handle h, const double* E, int64_t lde, int m, int n,
     Hr_w = Hr ? nullptr : a.take<double>((size_t)m * m);
     D_w = D ? nullptr : a.take<double>((size_t)m * m);
   });
-  if (s != VL_OK) return s;
+  if (s != VL_OK || x.measure) return s;
   if (!Hr) Hr = Hr_w;
   if (!D) D = D_w;
-  Ctx cx = make_ctx(h, gpart, part_cap);
-  cudaStream_t st = h->stream;
-  cov_and_stats<T>(h, cx, E, lde, m, n, o, scratch);
-  launch_pair_consts(o.C, m, rho32, c32, rho64, h->status, st);
+  vl_handle h = x.h;
+  Ctx cx = make_ctx(x, gpart, part_cap);
+  cudaStream_t st = x.s;
+  cov_and_stats<T>(cx, E, lde, m, n, o, scratch);
+  launch_pair_consts(o.C, m, rho32, c32, rho64, x.st, st);
   launch_transpose_std<T>(E, lde, m, n, o.mu, o.isd, xt, pl.m_pad, pl.n_pad, st);
   if (h->prof_start) cudaEventRecord(h->prof_start, st);
   if constexpr (sizeof(T) == 4)
-    launch_pairwise_f32(xt, pl, rho32, c32, pparts, st);
+    launch_pairwise_f32(xt, pl, rho32, c32, reinterpret_cast<float*>(pparts), st);
   else
     launch_pairwise_f64(xt, pl, rho64, pparts, st);
   if (h->prof_stop) cudaEventRecord(h->prof_stop, st);
@@ -220,7 +262,7 @@ vl_status pairwise_impl(vl_handle h, const double* E, int64_t lde, int m, int n,
 
 // ---------------------------------------------------------------- B0
 template <class T>
-vl_status fit_b_impl(vl_handle h, const double* E, int64_t lde, int m, int n,
+vl_status fit_b_impl(Exec& x, const double* E, int64_t lde, int m, int n,
                      const int32_t* order, const double* M, int p, double* B0, double* Btau,
                      const double* C_in) {
   const int nblk = (m + CHOL_NB - 1) / CHOL_NB;
@@ -229,7 +271,7 @@ vl_status fit_b_impl(vl_handle h, const double* E, int64_t lde, int m, int n,
   void* scratch = nullptr;
   T *Sp, *dinv, *R, *IBt = nullptr, *Mt = nullptr;
   double *IB, *gpart, *diag0;
-  vl_status s = with_workspace(h, [&](Arena& a) {
+  vl_status s = with_workspace(x, [&](Arena& a) {
     if (!C_in) {
       o.C = a.take<double>((size_t)m * m);
       o.mu = a.take<double>(m);
@@ -248,12 +290,12 @@ vl_status fit_b_impl(vl_handle h, const double* E, int64_t lde, int m, int n,
     }
     gpart = a.take<double>(part_cap);
   });
-  if (s != VL_OK) return s;
-  Ctx cx = make_ctx(h, gpart, part_cap);
-  cudaStream_t st = h->stream;
+  if (s != VL_OK || x.measure) return s;
+  Ctx cx = make_ctx(x, gpart, part_cap);
+  cudaStream_t st = x.s;
   const double* C = C_in;
   if (!C) {
-    cov_and_stats<T>(h, cx, E, lde, m, n, o, scratch);
+    cov_and_stats<T>(cx, E, lde, m, n, o, scratch);
     C = o.C;
   }
   launch_permute_cov<T>(C, m, 1.0 / n, order, Sp, m, st);
@@ -281,13 +323,144 @@ vl_status fit_b_impl(vl_handle h, const double* E, int64_t lde, int m, int n,
       }
     }
   }
-  return check_launch(h, "vl_fit_b");
+  return check_launch(x.h, "vl_fit_b");
+}
+
+vl_status order_impl(Exec& x, const double* D, int m, int32_t* order, double* gap) {
+  char* ows;
+  vl_status s = with_workspace(x, [&](Arena& a) { ows = a.take<char>(order_ws_bytes(m)); });
+  if (s != VL_OK || x.measure) return s;
+  launch_causal_order(D, m, ows, order, gap, x.st, x.s);
+  return check_launch(x.h, "vl_causal_order");
+}
+
+// The whole method on one series, on one execution context.  E, C and D are
+// per-series buffers of the caller (E: m x (n-p), C, D: m x m).
+template <class T>
+vl_status fit_one(Exec& x, const vl_instance& I, double* E, double* C, double* D) {
+  const int m = I.m, n_eff = I.n - I.p;
+  vl_status s = var_fit_impl<T>(x, I.X, I.ldx, m, I.n, I.p, I.M, E);
+  if (s == VL_OK) s = pairwise_impl<T>(x, E, n_eff, m, n_eff, nullptr, nullptr, D, C);
+  if (s == VL_OK) s = order_impl(x, D, m, I.order, nullptr);
+  if (s == VL_OK) s = fit_b_impl<T>(x, E, n_eff, m, n_eff, I.order, I.M, I.p, I.B0, I.Btau, C);
+  return s;
 }
 
 vl_status validate_prec(vl_handle h, vl_precision prec) {
   if (prec != VL_PREC_FP64 && prec != VL_PREC_MIXED)
     return fail(h, VL_ERR_ARG, "precision must be VL_PREC_FP64 or VL_PREC_MIXED");
   return VL_OK;
+}
+
+vl_status check_instance(vl_handle h, const vl_instance& I) {
+  if (!I.X || !I.order || !I.B0 || !I.M || !I.Btau)
+    return fail(h, VL_ERR_ARG, "vl_fit_batched: NULL pointer in instance");
+  if (I.m < 2 || I.p < 1 || I.n < 2 || I.m > VL_MAX_M || I.ldx < I.n)
+    return fail(h, VL_ERR_SHAPE, "vl_fit_batched: bad sizes");
+  if ((int64_t)I.n - I.p <= (int64_t)I.m * I.p + 1)
+    return fail(h, VL_ERR_RANK, "vl_fit_batched: n - p <= m p + 1");
+  return VL_OK;
+}
+
+// A batch: instances are dealt, largest first, to a pool of streams forked
+// from the handle's stream; every stream has its own workspace and per-series
+// buffers, and every instance its own status word.  Nothing allocates while
+// kernels are queued unless a buffer must grow; the host waits once, at the
+// end, to read the statuses.
+vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_precision prec,
+                       vl_status* inst_status) {
+  std::vector<int> idx;
+  for (int k = 0; k < count; ++k) {
+    inst_status[k] = check_instance(h, inst[k]);
+    if (inst_status[k] == VL_OK) idx.push_back(k);
+  }
+  // largest first (cost ~ m^2 n) so the streams finish together
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return (double)inst[a].m * inst[a].m * inst[a].n > (double)inst[b].m * inst[b].m * inst[b].n;
+  });
+  const int S = (int)std::min<size_t>(idx.size(), (size_t)BATCH_STREAMS);
+  vl_status err = VL_OK;
+  if (S > 0) {
+    // per-stream sizes: workspace of every step + E, C, D of its largest series
+    size_t ws_need = 0, buf_need = 0;
+    for (int k : idx) {
+      const vl_instance& I = inst[k];
+      Exec probe{h, nullptr, nullptr, nullptr, nullptr, true, 0};
+      double* dummy = nullptr;
+      if (prec == VL_PREC_MIXED)
+        fit_one<float>(probe, I, dummy, dummy, dummy);
+      else
+        fit_one<double>(probe, I, dummy, dummy, dummy);
+      ws_need = std::max(ws_need, probe.need);
+      const size_t m = I.m, ne = I.n - I.p;
+      buf_need = std::max(buf_need, sizeof(double) * (m * ne + 2 * m * m) + 1024);
+    }
+    vl_status s = VL_OK;
+    if ((int)h->pool.size() < S) h->pool.resize(S);
+    if (h->bstatus_cap < (size_t)count) {
+      if (h->bstatus) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->bstatus);
+      }
+      h->bstatus = nullptr;
+      h->bstatus_cap = 0;
+      if (cudaMalloc(&h->bstatus, sizeof(int) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, VL_ERR_NOMEM, "vl_fit_batched: status array allocation failed");
+      }
+      h->bstatus_cap = count;
+    }
+    for (int q = 0; q < S && s == VL_OK; ++q) {
+      PoolSlot& ps = h->pool[q];
+      if (!ps.stream && cudaStreamCreateWithFlags(&ps.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s = fail(h, VL_ERR_CUDA, "vl_fit_batched: stream creation failed");
+        break;
+      }
+      if (!ps.done && cudaEventCreateWithFlags(&ps.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        s = fail(h, VL_ERR_CUDA, "vl_fit_batched: event creation failed");
+        break;
+      }
+      s = grow(h, &ps.ws, &ps.ws_cap, ws_need, ps.stream);
+      if (s == VL_OK) s = grow(h, &ps.buf, &ps.buf_cap, buf_need, ps.stream);
+    }
+    if (s != VL_OK) return s;
+    cudaMemsetAsync(h->bstatus, 0, sizeof(int) * count, h->stream);
+    // fork: every pool stream waits for the handle stream
+    cudaEvent_t fork = h->pool[0].done;
+    cudaEventRecord(fork, h->stream);
+    for (int q = 0; q < S; ++q) cudaStreamWaitEvent(h->pool[q].stream, fork, 0);
+    for (size_t t = 0; t < idx.size(); ++t) {
+      const int k = idx[t];
+      PoolSlot& ps = h->pool[t % S];
+      const vl_instance& I = inst[k];
+      Exec x{h, ps.stream, h->bstatus + k, &ps.ws, &ps.ws_cap, false, 0};
+      double* E = static_cast<double*>(ps.buf);
+      double* C = E + (size_t)I.m * (I.n - I.p);
+      double* D = I.D ? I.D : C + (size_t)I.m * I.m;
+      vl_status r = prec == VL_PREC_MIXED ? fit_one<float>(x, I, E, C, D)
+                                          : fit_one<double>(x, I, E, C, D);
+      if (r != VL_OK) inst_status[k] = r;
+    }
+    // join
+    for (int q = 0; q < S; ++q) {
+      cudaEventRecord(h->pool[q].done, h->pool[q].stream);
+      cudaStreamWaitEvent(h->stream, h->pool[q].done, 0);
+    }
+    std::vector<int> dev(count, 0);
+    cudaError_t e = cudaMemcpyAsync(dev.data(), h->bstatus, sizeof(int) * count,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess)
+      return fail(h, VL_ERR_CUDA, std::string("vl_fit_batched: ") + cudaGetErrorString(e));
+    for (int k : idx)
+      if (inst_status[k] == VL_OK && dev[k] != 0) inst_status[k] = (vl_status)dev[k];
+  }
+  for (int k = 0; k < count; ++k)
+    if (err == VL_OK && inst_status[k] != VL_OK) err = inst_status[k];
+  if (err != VL_OK && h->last_error.empty()) h->last_error = "vl_fit_batched: an instance failed";
+  return err;
 }
 
 }  // namespace
@@ -330,6 +503,15 @@ vl_status vl_destroy(vl_handle h) {
   {
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
+    for (auto& ps : h->pool) {
+      if (ps.stream) cudaStreamSynchronize(ps.stream);
+      if (ps.ws) cudaFree(ps.ws);
+      if (ps.buf) cudaFree(ps.buf);
+      if (ps.done) cudaEventDestroy(ps.done);
+      if (ps.stream) cudaStreamDestroy(ps.stream);
+    }
+    if (h->bstatus) cudaFree(h->bstatus);
+    if (h->sbuf) cudaFree(h->sbuf);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
   }
@@ -402,8 +584,9 @@ vl_status vl_var_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, in
   if ((int64_t)n - p <= (int64_t)m * p + 1)
     return fail(h, VL_ERR_RANK, "vl_var_fit: n - p <= m p + 1, the VAR has no unique fit");
   DeviceGuard g(h->device);
-  return prec == VL_PREC_MIXED ? var_fit_impl<float>(h, X, ldx, m, n, p, M, E)
-                               : var_fit_impl<double>(h, X, ldx, m, n, p, M, E);
+  Exec x = handle_exec(h);
+  return prec == VL_PREC_MIXED ? var_fit_impl<float>(x, X, ldx, m, n, p, M, E)
+                               : var_fit_impl<double>(x, X, ldx, m, n, p, M, E);
 }
 
 vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
@@ -415,8 +598,9 @@ vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, 
   if (m < 2 || n_eff < 2 || m > VL_MAX_M || lde < n_eff)
     return fail(h, VL_ERR_SHAPE, "vl_pairwise_measure: need 2 <= m <= VL_MAX_M, n_eff >= 2, lde >= n_eff");
   DeviceGuard g(h->device);
-  return prec == VL_PREC_MIXED ? pairwise_impl<float>(h, E, lde, m, n_eff, Hx, Hr, D, nullptr)
-                               : pairwise_impl<double>(h, E, lde, m, n_eff, Hx, Hr, D, nullptr);
+  Exec x = handle_exec(h);
+  return prec == VL_PREC_MIXED ? pairwise_impl<float>(x, E, lde, m, n_eff, Hx, Hr, D, nullptr)
+                               : pairwise_impl<double>(x, E, lde, m, n_eff, Hx, Hr, D, nullptr);
 }
 
 vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, double* gap) {
@@ -424,11 +608,8 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
   if (!D || !order) return fail(h, VL_ERR_ARG, "vl_causal_order: D and order must not be NULL");
   if (m < 1 || m > VL_MAX_M) return fail(h, VL_ERR_SHAPE, "vl_causal_order: need 1 <= m <= VL_MAX_M");
   DeviceGuard g(h->device);
-  double* Pt;
-  vl_status s = with_workspace(h, [&](Arena& a) { Pt = a.take<double>((size_t)m * m); });
-  if (s != VL_OK) return s;
-  launch_causal_order(D, m, Pt, order, gap, h->status, h->stream);
-  return check_launch(h, "vl_causal_order");
+  Exec x = handle_exec(h);
+  return order_impl(x, D, m, order, gap);
 }
 
 vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
@@ -441,9 +622,29 @@ vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
     return fail(h, VL_ERR_SHAPE, "vl_fit_b: bad sizes");
   if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
   DeviceGuard g(h->device);
+  Exec x = handle_exec(h);
   return prec == VL_PREC_MIXED
-             ? fit_b_impl<float>(h, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr)
-             : fit_b_impl<double>(h, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr);
+             ? fit_b_impl<float>(x, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr)
+             : fit_b_impl<double>(x, E, lde, m, n_eff, order, M, p, B0, Btau, nullptr);
+}
+
+vl_status vl_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, int p,
+                 vl_precision prec, double* M, int32_t* order, double* B0, double* Btau,
+                 double* D) {
+  if (!h) return VL_ERR_ARG;
+  if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
+  vl_instance I{X, ldx, m, n, p, order, B0, Btau, M, D};
+  vl_status s = check_instance(h, I);
+  if (s != VL_OK) return s;
+  DeviceGuard g(h->device);
+  const size_t mm = (size_t)m * m, ne = (size_t)(n - p);
+  s = grow(h, &h->sbuf, &h->sbuf_cap, sizeof(double) * (m * ne + 2 * mm) + 1024, h->stream);
+  if (s != VL_OK) return s;
+  double* E = static_cast<double*>(h->sbuf);
+  double* C = E + m * ne;
+  if (!D) D = C + mm;
+  Exec x = handle_exec(h);
+  return prec == VL_PREC_MIXED ? fit_one<float>(x, I, E, C, D) : fit_one<double>(x, I, E, C, D);
 }
 
 vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_precision prec,
@@ -452,58 +653,9 @@ vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_pre
   if (count < 0 || (count > 0 && (!inst || !inst_status)))
     return fail(h, VL_ERR_ARG, "vl_fit_batched: inst and inst_status must not be NULL");
   if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
+  if (count == 0) return VL_OK;
   DeviceGuard g(h->device);
-  vl_status first = VL_OK;
-  for (int k = 0; k < count; ++k) {
-    const vl_instance& I = inst[k];
-    vl_status s = VL_OK;
-    if (!I.X || !I.order || !I.B0 || !I.M || (I.p > 0 && !I.Btau))
-      s = fail(h, VL_ERR_ARG, "vl_fit_batched: NULL pointer in instance");
-    else if (I.m < 2 || I.p < 1 || I.n < 2 || I.m > VL_MAX_M || I.ldx < I.n)
-      s = fail(h, VL_ERR_SHAPE, "vl_fit_batched: bad sizes");
-    else if ((int64_t)I.n - I.p <= (int64_t)I.m * I.p + 1)
-      s = fail(h, VL_ERR_RANK, "vl_fit_batched: n - p <= m p + 1");
-    if (s == VL_OK) {
-      const int m = I.m, n_eff = I.n - I.p;
-      // per-instance buffers that the caller does not provide live at the
-      // top of the workspace growth: allocate them separately
-      double *E = nullptr, *D = I.D, *C = nullptr;
-      size_t bytes = sizeof(double) * ((size_t)m * n_eff + (I.D ? 0 : (size_t)m * m) + (size_t)m * m);
-      void* blk = nullptr;
-      if (cudaMalloc(&blk, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        s = fail(h, VL_ERR_NOMEM, "vl_fit_batched: instance buffer allocation failed");
-      } else {
-        E = static_cast<double*>(blk);
-        C = E + (size_t)m * n_eff;
-        if (!D) D = C + (size_t)m * m;
-        if (prec == VL_PREC_MIXED) {
-          s = var_fit_impl<float>(h, I.X, I.ldx, m, I.n, I.p, I.M, E);
-          if (s == VL_OK) s = pairwise_impl<float>(h, E, n_eff, m, n_eff, nullptr, nullptr, D, C);
-        } else {
-          s = var_fit_impl<double>(h, I.X, I.ldx, m, I.n, I.p, I.M, E);
-          if (s == VL_OK) s = pairwise_impl<double>(h, E, n_eff, m, n_eff, nullptr, nullptr, D, C);
-        }
-        if (s == VL_OK) {
-          double* Pt;
-          s = with_workspace(h, [&](Arena& a) { Pt = a.take<double>((size_t)m * m); });
-          if (s == VL_OK) launch_causal_order(D, m, Pt, I.order, nullptr, h->status, h->stream);
-        }
-        if (s == VL_OK) {
-          if (prec == VL_PREC_MIXED)
-            s = fit_b_impl<float>(h, E, n_eff, m, n_eff, I.order, I.M, I.p, I.B0, I.Btau, C);
-          else
-            s = fit_b_impl<double>(h, E, n_eff, m, n_eff, I.order, I.M, I.p, I.B0, I.Btau, C);
-        }
-        vl_status sy = vl_sync(h);
-        if (s == VL_OK) s = sy;
-        cudaFree(blk);
-      }
-    }
-    inst_status[k] = s;
-    if (first == VL_OK && s != VL_OK) first = s;
-  }
-  return first;
+  return batched_impl(h, inst, count, prec, inst_status);
 }
 
 }  // extern "C"

@@ -14,8 +14,8 @@ namespace vl {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, KC = 16, NTH = 256;
-constexpr int kFlush = 256;
+constexpr int NTH = 256;
+constexpr int KC = 8;  // k-depth of one shared-memory stage
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   float s = hi + x;
@@ -25,94 +25,178 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo += err;
 }
 
-template <class T>
-__device__ __forceinline__ void load_tile(T (*sm)[TM + 4], View<T> v, int r0, int rows, int k0,
-                                          int kmax) {
-  // sm[k][r] = v(r0 + r, k0 + k), zero outside.
-  if (v.ks == 1) {
-    for (int idx = threadIdx.x; idx < TM * KC; idx += NTH) {
-      int r = idx / KC, k = idx % KC;
-      int gr = r0 + r, gk = k0 + k;
-      sm[k][r] = (gr < rows && gk < kmax) ? v.base[(int64_t)gr * v.rs + gk] : T(0);
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < TM * KC; idx += NTH) {
-      int r = idx % TM, k = idx / TM;
-      int gr = r0 + r, gk = k0 + k;
-      sm[k][r] = (gr < rows && gk < kmax) ? v.base[(int64_t)gr * v.rs + (int64_t)gk * v.ks]
-                                          : T(0);
+// Reciprocal and square root for the factorisations: the single-instruction
+// approximations in FP32 (a few ulp; the FP32 factorisation's own rounding
+// dominates), IEEE in FP64.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
+
+// Register-staged loads of one BM x KC stage of a view.  With ks == 1
+// consecutive threads read consecutive k of a row, otherwise consecutive rows.
+template <class T, int BM>
+struct StageLoader {
+  static constexpr int PER = BM * KC / NTH;
+  T v[PER];
+  __device__ __forceinline__ static void slot(int idx, int ks, int& r, int& k) {
+    if (ks == 1) {
+      r = idx / KC;
+      k = idx % KC;
+    } else {
+      r = idx % BM;
+      k = idx / BM;
     }
   }
-}
+  __device__ __forceinline__ void load(const View<T>& w, int r0, int rows, int k0, int kmax) {
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      int r, k;
+      slot(threadIdx.x + e * NTH, w.ks, r, k);
+      const int gr = r0 + r, gk = k0 + k;
+      v[e] = (gr < rows && gk < kmax) ? w.base[(int64_t)gr * w.rs + (int64_t)gk * w.ks] : T(0);
+    }
+  }
+  __device__ __forceinline__ void store(T* sm, int ks) const {  // sm[k * (BM + 4) + r]
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      int r, k;
+      slot(threadIdx.x + e * NTH, ks, r, k);
+      sm[k * (BM + 4) + r] = v[e];
+    }
+  }
+};
 
-// mode: 0 = full, 1 = lower (c <= r), 2 = upper (c >= r, mirrored into C[c, r])
-template <class T, class TC>
+// mode: 0 = full, 1 = lower (c <= r), 2 = upper (c >= r, mirrored into C[c, r]).
+// C[r, c] = alpha * sum_k A(r, k) B(c, k) + beta * C[r, c], or, with split-K
+// (gridDim.z > 1), slice z's partial into part[z][r][c].  The next k-stage is
+// loaded into registers while the current one is consumed (double buffer).
+// SPLIT: A and B come as (hi, lo) FP32 pairs; each step adds hi*hi + hi*lo +
+// lo*hi and the FP32 sum is flushed every 32 steps into a double-float pair.
+template <class T, class TC, int TMt, int TNt, bool SPLIT>
 __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, int kchunk,
-                                                   double alpha, View<T> A, View<T> B,
-                                                   double beta, TC* __restrict__ C,
+                                                   double alpha, View<T> A, View<T> Al, View<T> B,
+                                                   View<T> Bl, double beta, TC* __restrict__ C,
                                                    int64_t ldc, int mode,
                                                    double* __restrict__ part) {
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  if (mode == 1 && c0 > r0 + TM - 1) return;
-  if (mode == 2 && r0 > c0 + TN - 1) return;
-  __shared__ __align__(16) T As[KC][TM + 4];
-  __shared__ __align__(16) T Bs[KC][TN + 4];
+  constexpr int BM = 16 * TMt, BN = 16 * TNt;
+  constexpr int NOP = SPLIT ? 2 : 1;
+  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+  if (mode == 1 && c0 > r0 + BM - 1) return;
+  if (mode == 2 && r0 > c0 + BN - 1) return;
+  __shared__ __align__(16) T As[2][NOP][KC * (BM + 4)];
+  __shared__ __align__(16) T Bs[2][NOP][KC * (BN + 4)];
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  T acc[4][4];
-  float hi[4][4], lo[4][4];
+  T acc[TMt][TNt];
+  float hi[SPLIT ? TMt : 1][SPLIT ? TNt : 1], lo[SPLIT ? TMt : 1][SPLIT ? TNt : 1];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < TMt; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      acc[a][b] = T(0);
-      hi[a][b] = 0.f;
-      lo[a][b] = 0.f;
+    for (int b = 0; b < TNt; ++b) acc[a][b] = T(0);
+  if constexpr (SPLIT) {
+#pragma unroll
+    for (int a = 0; a < TMt; ++a)
+#pragma unroll
+      for (int b = 0; b < TNt; ++b) hi[a][b] = lo[a][b] = 0.f;
+  }
+  StageLoader<T, BM> la, lal;
+  StageLoader<T, BN> lb, lbl;
+  const int nst = kend > kbeg ? (kend - kbeg + KC - 1) / KC : 0;
+  if (nst > 0) {
+    la.load(A, r0, M, kbeg, kend);
+    lb.load(B, c0, N, kbeg, kend);
+    la.store(As[0][0], A.ks);
+    lb.store(Bs[0][0], B.ks);
+    if constexpr (SPLIT) {
+      lal.load(Al, r0, M, kbeg, kend);
+      lbl.load(Bl, c0, N, kbeg, kend);
+      lal.store(As[0][NOP - 1], Al.ks);
+      lbl.store(Bs[0][NOP - 1], Bl.ks);
     }
-  int since_flush = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += KC) {
-    load_tile<T>(As, A, r0, M, k0, kend);
-    load_tile<T>(Bs, B, c0, N, k0, kend);
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int t = 0; t < nst; ++t) {
+    const int buf = t & 1;
+    const bool more = t + 1 < nst;
+    if (more) {
+      const int k1 = kbeg + (t + 1) * KC;
+      la.load(A, r0, M, k1, kend);
+      lb.load(B, c0, N, k1, kend);
+      if constexpr (SPLIT) {
+        lal.load(Al, r0, M, k1, kend);
+        lbl.load(Bl, c0, N, k1, kend);
+      }
+    }
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      T a[4], b[4];
+      T a[TMt], b[TNt];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty * 4 + q];
-        b[q] = Bs[kk][tx * 4 + q];
+      for (int q = 0; q < TMt; ++q) a[q] = As[buf][0][kk * (BM + 4) + ty * TMt + q];
+#pragma unroll
+      for (int q = 0; q < TNt; ++q) b[q] = Bs[buf][0][kk * (BN + 4) + tx * TNt + q];
+      if constexpr (SPLIT) {
+        T al[TMt], bl[TNt];
+#pragma unroll
+        for (int q = 0; q < TMt; ++q) al[q] = As[buf][NOP - 1][kk * (BM + 4) + ty * TMt + q];
+#pragma unroll
+        for (int q = 0; q < TNt; ++q) bl[q] = Bs[buf][NOP - 1][kk * (BN + 4) + tx * TNt + q];
+#pragma unroll
+        for (int x = 0; x < TMt; ++x)
+#pragma unroll
+          for (int y = 0; y < TNt; ++y) {
+            T tt = fma(a[x], bl[y], al[x] * b[y]);
+            acc[x][y] = fma(a[x], b[y], acc[x][y] + tt);
+          }
+      } else {
+#pragma unroll
+        for (int x = 0; x < TMt; ++x)
+#pragma unroll
+          for (int y = 0; y < TNt; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
       }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
     }
-    __syncthreads();
-    if constexpr (sizeof(T) == 4) {
-      since_flush += KC;
-      if (since_flush >= kFlush) {
-        since_flush = 0;
+    if constexpr (SPLIT) {
+      if ((t & 3) == 3) {  // every 32 steps of k
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+        for (int x = 0; x < TMt; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) {
+          for (int y = 0; y < TNt; ++y) {
             two_sum_acc(hi[x][y], lo[x][y], (float)acc[x][y]);
             acc[x][y] = T(0);
           }
       }
     }
+    if (more) {
+      la.store(As[buf ^ 1][0], A.ks);
+      lb.store(Bs[buf ^ 1][0], B.ks);
+      if constexpr (SPLIT) {
+        lal.store(As[buf ^ 1][NOP - 1], Al.ks);
+        lbl.store(Bs[buf ^ 1][NOP - 1], Bl.ks);
+      }
+    }
+    __syncthreads();
   }
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < TMt; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int r = r0 + ty * 4 + x, c = c0 + tx * 4 + y;
+    for (int y = 0; y < TNt; ++y) {
+      const int r = r0 + ty * TMt + x, c = c0 + tx * TNt + y;
       if (r >= M || c >= N) continue;
       if (mode == 1 && c > r) continue;
       if (mode == 2 && c < r) continue;
+      if constexpr (!SPLIT && sizeof(TC) == 4 && sizeof(T) == 4) {
+        // all-FP32 epilogue: FP64 conversions run at 1/64 rate on this part
+        if (!part) {
+          float v = (float)alpha * acc[x][y];
+          if (beta != 0.0) v = fmaf((float)beta, C[(int64_t)r * ldc + c], v);
+          C[(int64_t)r * ldc + c] = v;
+          if (mode == 2 && c != r) C[(int64_t)c * ldc + r] = v;
+          continue;
+        }
+      }
       double v;
-      if constexpr (sizeof(T) == 4)
+      if constexpr (SPLIT)
         v = ((double)hi[x][y] + (double)lo[x][y]) + (double)acc[x][y];
       else
         v = (double)acc[x][y];
@@ -142,84 +226,13 @@ __global__ void splitk_reduce_kernel(const double* __restrict__ part, int ksplit
   if (mode == 2 && c != r) C[(int64_t)c * ldc + r] = (TC)v;
 }
 
-// Compensated covariance product: (Ahi + Alo)(Bhi + Blo)^T ~ Ahi Bhi + Ahi Blo
-// + Alo Bhi, FP32 FMAs flushed every 32 steps into a double-float accumulator.
-__global__ void __launch_bounds__(NTH) gemm_split_kernel(int M, int N, int K, int kchunk,
-                                                         View<float> Ah, View<float> Al,
-                                                         View<float> Bh, View<float> Bl,
-                                                         double* __restrict__ C, int64_t ldc,
-                                                         int mode, double* __restrict__ part) {
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  if (mode == 2 && r0 > c0 + TN - 1) return;
-  __shared__ __align__(16) float Ahs[KC][TM + 4], Als[KC][TM + 4];
-  __shared__ __align__(16) float Bhs[KC][TN + 4], Bls[KC][TN + 4];
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  const int kbeg = blockIdx.z * kchunk;
-  const int kend = min(K, kbeg + kchunk);
-  float acc[4][4], hi[4][4], lo[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
-  int since = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += KC) {
-    load_tile<float>(Ahs, Ah, r0, M, k0, kend);
-    load_tile<float>(Als, Al, r0, M, k0, kend);
-    load_tile<float>(Bhs, Bh, c0, N, k0, kend);
-    load_tile<float>(Bls, Bl, c0, N, k0, kend);
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < KC; ++kk) {
-      float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        ah[q] = Ahs[kk][ty * 4 + q];
-        al[q] = Als[kk][ty * 4 + q];
-        bh[q] = Bhs[kk][tx * 4 + q];
-        bl[q] = Bls[kk][tx * 4 + q];
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          float t = fmaf(ah[x], bl[y], al[x] * bh[y]);
-          acc[x][y] = fmaf(ah[x], bh[y], acc[x][y] + t);
-        }
-    }
-    __syncthreads();
-    since += KC;
-    if (since >= 32) {
-      since = 0;
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          two_sum_acc(hi[x][y], lo[x][y], acc[x][y]);
-          acc[x][y] = 0.f;
-        }
-    }
-  }
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int r = r0 + ty * 4 + x, c = c0 + tx * 4 + y;
-      if (r >= M || c >= N) continue;
-      if (mode == 2 && c < r) continue;
-      double v = ((double)hi[x][y] + (double)lo[x][y]) + (double)acc[x][y];
-      if (part) {
-        part[((int64_t)blockIdx.z * M + r) * N + c] = v;
-      } else {
-        C[(int64_t)r * ldc + c] = v;
-        if (mode == 2 && c != r) C[(int64_t)c * ldc + r] = v;
-      }
-    }
-}
-
-// ---- Cholesky of one nb x nb diagonal block in shared memory, plus the
-// inverse of the factor.
-// A pivot below rel_tol times the matrix's original diagonal entry marks the
-// system as (numerically) singular.
+// ---- Cholesky of one nb x nb diagonal block, plus the inverse of the factor.
+// Right-looking elimination with the block in registers: thread (ty, tx)
+// owns rows 4ty..4ty+3 x columns 4tx..4tx+3.  At step j the owners of column j
+// publish it (unscaled) to a double-buffered shared vector, one barrier, then
+// every thread updates its own elements a_ik -= a_ij a_kj / a_jj (j < k <= i)
+// and the owners scale column j by 1/sqrt(a_jj).  The factor then goes to
+// shared memory for the inverse, which is built row by row.
 template <class T>
 __global__ void __launch_bounds__(NTH) chol_diag_kernel(T* __restrict__ A, int64_t lda, int nb,
                                                         T* __restrict__ dinv,
@@ -228,54 +241,245 @@ __global__ void __launch_bounds__(NTH) chol_diag_kernel(T* __restrict__ A, int64
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T(*L)[CHOL_NB + 1] = reinterpret_cast<T(*)[CHOL_NB + 1]>(chol_smem);
   T(*Li)[CHOL_NB + 1] = L + CHOL_NB;
+  __shared__ T colj[2][CHOL_NB];
+  __shared__ T thr[CHOL_NB];
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int idx = threadIdx.x; idx < CHOL_NB * CHOL_NB; idx += NTH) {
-    int r = idx / CHOL_NB, c = idx % CHOL_NB;
-    T v = T(0);
-    if (r < nb && c <= r) v = A[(int64_t)r * lda + c];
-    if (r >= nb && r == c) v = T(1);  // pad with identity
-    L[r][c] = v;
-    Li[r][c] = T(0);
-  }
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      T d = L[j][j];
-      if (!((double)d > rel_tol * diag0[j])) {
-        bad = 1;
-        d = T(1);
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  if (tid == 0) bad = 0;
+  // pivot thresholds, converted once (FP64 issues at 1/64 rate on this part)
+  if (tid < CHOL_NB) thr[tid] = tid < nb ? (T)(rel_tol * diag0[tid]) : T(0);
+  T r[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty * 4 + a, k = tx * 4 + b;
+      T v = T(0);
+      if (i < nb && k <= i) v = A[(int64_t)i * lda + k];
+      if (i >= nb && i == k) v = T(1);  // pad with identity
+      r[a][b] = v;
+    }
+  for (int j = 0; j < CHOL_NB; ++j) {
+    const int buf = j & 1;
+    if (tx == (j >> 2)) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T v = r[a][0];
+#pragma unroll
+        for (int b = 1; b < 4; ++b)
+          if ((j & 3) == b) v = r[a][b];
+        colj[buf][ty * 4 + a] = v;
       }
-      L[j][j] = sqrt(d);
     }
     __syncthreads();
-    const T dj = L[j][j];
-    for (int i = j + 1 + threadIdx.x; i < nb; i += NTH) L[i][j] /= dj;
-    __syncthreads();
-    // trailing update of the lower triangle (i >= k > j)
-    const int w = nb - j - 1;
-    for (int idx = threadIdx.x; idx < w * w; idx += NTH) {
-      int i = j + 1 + idx / w, k = j + 1 + idx % w;
-      if (k <= i) L[i][k] -= L[i][j] * L[k][j];
+    T d = colj[buf][j];
+    bool ok = d > thr[j];
+    if (!ok) d = T(1);
+    if (!ok && tid == 0 && j < nb) bad = 1;
+    const T inv_d = recip(d);
+    T ci[4], ck[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ci[q] = colj[buf][ty * 4 + q];
+      ck[q] = colj[buf][tx * 4 + q];
     }
-    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = ty * 4 + a;
+      const T lij = ci[a] * inv_d;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int k = tx * 4 + b;
+        if (k > j && k <= i) r[a][b] -= lij * ck[b];
+      }
+    }
+    if (tx == (j >> 2)) {
+      const T pv = sqrt_fast(d);
+      const T ipv = recip(pv);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = ty * 4 + a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if ((j & 3) != b) continue;
+          if (i > j) r[a][b] *= ipv;
+          if (i == j) r[a][b] = pv;
+        }
+      }
+    }
   }
-  if (threadIdx.x == 0 && bad) set_status(st, VL_ERR_RANK);
-  // inverse of the lower-triangular factor: column c of L^{-1} by forward
-  // substitution, one thread per column
-  for (int c = threadIdx.x; c < CHOL_NB; c += NTH) {
-    for (int i = 0; i < CHOL_NB; ++i) {
-      T s = (i == c) ? T(1) : T(0);
-      for (int k = c; k < i; ++k) s -= L[i][k] * Li[k][c];
-      Li[i][c] = (i >= c) ? s / L[i][i] : T(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty * 4 + a, k = tx * 4 + b;
+      L[i][k] = k <= i ? r[a][b] : T(0);
     }
-  }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < CHOL_NB * CHOL_NB; idx += NTH) {
+  if (tid == 0 && bad) set_status(st, VL_ERR_RANK);
+  // Li = L^{-1}: row i from rows < i, every column c <= i in parallel:
+  // Li[i][c] = (delta_ic - sum_{c <= k < i} L[i][k] Li[k][c]) / L[i][i]
+  // 4 threads per column split the k range and combine with shuffles.
+  const int col = tid >> 2, part = tid & 3;
+  for (int i = 0; i < CHOL_NB; ++i) {
+    T sacc = T(0);
+    if (col < i) {
+      for (int k = col + part; k < i; k += 4) sacc += L[i][k] * Li[k][col];
+    }
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+    if (part == 0) {
+      const T rdiag = recip(L[i][i]);
+      if (col < i)
+        Li[i][col] = -sacc * rdiag;
+      else if (col == i)
+        Li[i][col] = rdiag;
+      else
+        Li[i][col] = T(0);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < CHOL_NB * CHOL_NB; idx += NTH) {
     int r = idx / CHOL_NB, c = idx % CHOL_NB;
     if (r < nb && c <= r) A[(int64_t)r * lda + c] = L[r][c];
     dinv[idx] = Li[r][c];
   }
+}
+
+// ---- Column-parallel blocked triangular solves.  Each CTA owns SC
+// right-hand-side columns and sweeps all block rows: forward
+//     Y_b = Linv_bb (R_b - L_{b,<b} Y_{<b}),
+// then (optionally) backward
+//     X_b = Linv_bb^T (Y_b - L_{>b,b}^T X_{>b}),
+// streaming 64 x 64 pieces of L (and the matching rows of R) through shared
+// memory with cp.async, double-buffered so a piece loads while the previous
+// one is consumed.  Results overwrite R.
+constexpr int SC = 8;
+constexpr int LSW = CHOL_NB + 1;  // padded row of a shared L piece
+
+template <class T>
+__device__ __forceinline__ void cp_async_el(T* smem, const T* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <class T>
+__global__ void __launch_bounds__(NTH) trsm_cols_kernel(const T* __restrict__ L, int64_t lda,
+                                                        const T* __restrict__ dinv, int n,
+                                                        T* __restrict__ R, int64_t ldr, int nrhs,
+                                                        int backward) {
+  extern __shared__ __align__(16) unsigned char trsm_smem[];
+  T* Lbuf = reinterpret_cast<T*>(trsm_smem);          // [2][64][LSW]
+  T* Dbuf = Lbuf + 2 * CHOL_NB * LSW;                  // [64][LSW]  inverse block
+  T* Ybuf = Dbuf + CHOL_NB * LSW;                      // [2][64][SC]
+  T* Acc = Ybuf + 2 * CHOL_NB * SC;                    // [64][SC]
+  const int tid = threadIdx.x;
+  const int r = tid >> 2;        // row within the block, 0..63
+  const int cc = (tid & 3) * 2;  // two columns per thread
+  const int c0 = blockIdx.x * SC;
+  const int nblk = (n + CHOL_NB - 1) / CHOL_NB;
+  for (int pass = 0; pass < (backward ? 2 : 1); ++pass) {
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int b = pass == 0 ? bi : nblk - 1 - bi;
+      const int k0 = b * CHOL_NB;
+      const int nb = min(CHOL_NB, n - k0);
+      const int jb = pass == 0 ? 0 : k0 + nb;  // forward 0..k0, backward k0+nb..n
+      const int je = pass == 0 ? k0 : n;
+      const int nch = (je - jb + CHOL_NB - 1) / CHOL_NB;
+      // issue piece c into buffer c & 1 (zero outside the matrix)
+      auto issue = [&](int c) {
+        const int j0 = jb + c * CHOL_NB;
+        const int jn = min(CHOL_NB, je - j0);
+        T* Ls = Lbuf + (c & 1) * CHOL_NB * LSW;
+        T* Ys = Ybuf + (c & 1) * CHOL_NB * SC;
+        for (int idx = tid; idx < CHOL_NB * CHOL_NB; idx += NTH) {
+          const int a = idx / CHOL_NB, bc = idx % CHOL_NB;
+          if (pass == 0) {  // Ls[a][bc] = L[k0 + a][j0 + bc]
+            if (a < nb && bc < jn)
+              cp_async_el(&Ls[a * LSW + bc], &L[(int64_t)(k0 + a) * lda + j0 + bc]);
+            else
+              Ls[a * LSW + bc] = T(0);
+          } else {  // Ls[bc][a] = L[j0 + a][k0 + bc]  (transposed slab)
+            if (a < jn && bc < nb)
+              cp_async_el(&Ls[bc * LSW + a], &L[(int64_t)(j0 + a) * lda + k0 + bc]);
+            else
+              Ls[bc * LSW + a] = T(0);
+          }
+        }
+        for (int idx = tid; idx < CHOL_NB * SC; idx += NTH) {
+          const int a = idx / SC, c = idx % SC;
+          if (a < jn && c0 + c < nrhs)
+            cp_async_el(&Ys[a * SC + c], &R[(int64_t)(j0 + a) * ldr + c0 + c]);
+          else
+            Ys[a * SC + c] = T(0);
+        }
+      };
+      // the inverse of the diagonal block (transposed for the backward pass)
+      // travels with the first piece
+      for (int idx = tid; idx < CHOL_NB * CHOL_NB; idx += NTH) {
+        const int a = idx / CHOL_NB, bc = idx % CHOL_NB;
+        T* dst = pass == 0 ? &Dbuf[a * LSW + bc] : &Dbuf[bc * LSW + a];
+        cp_async_el(dst, &dinv[(int64_t)b * CHOL_NB * CHOL_NB + idx]);
+      }
+      T acc[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int col = c0 + cc + q;
+        acc[q] = (r < nb && col < nrhs) ? R[(int64_t)(k0 + r) * ldr + col] : T(0);
+      }
+      if (nch > 0) issue(0);
+      cp_commit();
+      for (int c = 0; c < nch; ++c) {
+        if (c + 1 < nch) {
+          issue(c + 1);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncthreads();
+        const T* Ls = Lbuf + (c & 1) * CHOL_NB * LSW;
+        const T* Ys = Ybuf + (c & 1) * CHOL_NB * SC;
+#pragma unroll 8
+        for (int jj = 0; jj < CHOL_NB; ++jj) {
+          const T l = Ls[r * LSW + jj];
+          acc[0] -= l * Ys[jj * SC + cc];
+          acc[1] -= l * Ys[jj * SC + cc + 1];
+        }
+        __syncthreads();
+      }
+      cp_wait<0>();
+      Acc[r * SC + cc] = acc[0];
+      Acc[r * SC + cc + 1] = acc[1];
+      __syncthreads();
+      T o0 = T(0), o1 = T(0);
+#pragma unroll 8
+      for (int q = 0; q < CHOL_NB; ++q) {
+        const T l = Dbuf[r * LSW + q];
+        o0 += l * Acc[q * SC + cc];
+        o1 += l * Acc[q * SC + cc + 1];
+      }
+      if (r < nb) {
+        if (c0 + cc < nrhs) R[(int64_t)(k0 + r) * ldr + c0 + cc] = o0;
+        if (c0 + cc + 1 < nrhs) R[(int64_t)(k0 + r) * ldr + c0 + cc + 1] = o1;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <class T>
+size_t trsm_smem_bytes() {
+  return sizeof(T) * (3 * CHOL_NB * LSW + 3 * CHOL_NB * SC);
 }
 
 template <class TI, class TO>
@@ -302,46 +506,61 @@ __global__ void set_identity_kernel(T* A, int64_t lda, int n) {
   A[(int64_t)r * lda + c] = (r == c) ? T(1) : T(0);
 }
 
-int pick_ksplit(int M, int N, int K, int mode, int num_sms) {
-  int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-  if (mode != 0) tiles = (tiles + ((M + TM - 1) / TM)) / 2;
+// Split-K factor: about two CTAs per SM, FP32 slices of at most max_chunk
+// steps of k (the FP64 reduction of the slices bounds the accumulation error).
+int pick_ksplit(int tiles, int K, int num_sms, int max_chunk) {
   int want = std::max(1, 2 * num_sms / std::max(tiles, 1));
-  int maxk = std::max(1, K / 512);
-  return std::min(std::min(want, maxk), 16);
+  int need = (K + max_chunk - 1) / max_chunk;
+  int ks = std::max(want, need);
+  ks = std::min(ks, std::max(1, K / 64));
+  return std::min(ks, 64);
+}
+
+template <class T, class TC, int TMt, int TNt, bool SPLIT>
+void gemm_launch(const Ctx& cx, int M, int N, int K, double alpha, View<T> A, View<T> Al,
+                 View<T> B, View<T> Bl, double beta, TC* C, int64_t ldc, int mode,
+                 int max_chunk) {
+  if (M <= 0 || N <= 0) return;
+  constexpr int BM = 16 * TMt, BN = 16 * TNt;
+  const int gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
+  int tiles = gm * gn;
+  if (mode != 0) tiles = (tiles + std::min(gm, gn)) / 2;
+  int ks = pick_ksplit(tiles, K, cx.num_sms, max_chunk);
+  if (ks > 1 && (!cx.part || (size_t)ks * M * N > cx.part_cap))
+    ks = cx.part ? std::max(1, (int)std::min<size_t>(ks, cx.part_cap / ((size_t)M * N))) : 1;
+  int kchunk = ks > 1 ? (((K + ks - 1) / ks + 31) / 32) * 32 : std::max(K, 1);
+  ks = ks > 1 ? (K + kchunk - 1) / kchunk : 1;
+  dim3 grid(gn, gm, ks);
+  note_launch();
+  gemm_kernel<T, TC, TMt, TNt, SPLIT><<<grid, NTH, 0, cx.s>>>(
+      M, N, K, kchunk, alpha, A, Al, B, Bl, beta, C, ldc, mode, ks > 1 ? cx.part : nullptr);
+  if (ks > 1) {
+    int64_t tot = (int64_t)M * N;
+    note_launch();
+    splitk_reduce_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, cx.s>>>(
+        cx.part, ks, M, N, beta, C, ldc, mode);
+  }
 }
 
 }  // namespace
 
 size_t gemm_part_need(int M, int N, int K) {
   (void)K;
-  return (size_t)16 * M * N;
+  return (size_t)64 * M * N;
 }
 
 template <class T, class TC>
 void launch_gemm(const Ctx& cx, int M, int N, int K, double alpha, View<T> A, View<T> B,
                  double beta, TC* C, int64_t ldc, bool lower_only) {
-  if (M <= 0 || N <= 0) return;
-  cudaStream_t s = cx.s;
   const int mode = lower_only ? 1 : 0;
-  int ks = pick_ksplit(M, N, K, mode, cx.num_sms);
-  double* part = nullptr;
-  if (ks > 1) {
-    if ((size_t)ks * M * N <= cx.part_cap && cx.part)
-      part = cx.part;
+  if constexpr (sizeof(T) == 4) {
+    if ((int64_t)M * N >= 256 * 256)
+      gemm_launch<T, TC, 8, 8, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
     else
-      ks = 1;
-  }
-  int kchunk = ks > 1 ? (((K + ks - 1) / ks + KC - 1) / KC) * KC : std::max(K, 1);
-  ks = ks > 1 ? (K + kchunk - 1) / kchunk : 1;
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, ks);
-  note_launch();
-  gemm_kernel<T, TC><<<grid, NTH, 0, s>>>(M, N, K, kchunk, alpha, A, B, beta, C, ldc, mode,
-                                          ks > 1 ? part : nullptr);
-  if (ks > 1) {
-    int64_t tot = (int64_t)M * N;
-    note_launch();
-    splitk_reduce_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, ks, M, N, beta,
-                                                                          C, ldc, mode);
+      gemm_launch<T, TC, 4, 4, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
+  } else {
+    gemm_launch<T, TC, 4, 4, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode,
+                                    1 << 30);
   }
 }
 template void launch_gemm<float, float>(const Ctx&, int, int, int, double, View<float>,
@@ -354,28 +573,8 @@ template void launch_gemm<double, double>(const Ctx&, int, int, int, double, Vie
 void launch_gemm_split(const Ctx& cx, int M, int N, int K, View<float> Ahi, View<float> Alo,
                        View<float> Bhi, View<float> Blo, double* C, int64_t ldc,
                        bool upper_only) {
-  cudaStream_t s = cx.s;
-  const int mode = upper_only ? 2 : 0;
-  int ks = pick_ksplit(M, N, K, mode, cx.num_sms);
-  double* part = nullptr;
-  if (ks > 1) {
-    if ((size_t)ks * M * N <= cx.part_cap && cx.part)
-      part = cx.part;
-    else
-      ks = 1;
-  }
-  int kchunk = ks > 1 ? (((K + ks - 1) / ks + 31) / 32) * 32 : std::max(K, 1);
-  ks = ks > 1 ? (K + kchunk - 1) / kchunk : 1;
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, ks);
-  note_launch();
-  gemm_split_kernel<<<grid, NTH, 0, s>>>(M, N, K, kchunk, Ahi, Alo, Bhi, Blo, C, ldc, mode,
-                                         ks > 1 ? part : nullptr);
-  if (ks > 1) {
-    int64_t tot = (int64_t)M * N;
-    note_launch();
-    splitk_reduce_kernel<double><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-        part, ks, M, N, 0.0, C, ldc, mode);
-  }
+  gemm_launch<float, double, 4, 4, true>(cx, M, N, K, 1.0, Ahi, Alo, Bhi, Blo, 0.0, C, ldc,
+                                         upper_only ? 2 : 0, 1 << 30);
 }
 
 template <class T>
@@ -417,33 +616,16 @@ template void chol_blocked<double>(const Ctx&, double*, int64_t, int, double*, d
 template <class T>
 void chol_solve_blocked(const Ctx& cx, const T* L, int64_t lda, const T* dinv, int n, T* R,
                         int64_t ldr, int nrhs, bool backward) {
-  const int NB = CHOL_NB;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int nb = std::min(NB, n - k0);
-    if (k0 > 0) {
-      View<T> Lr{L + (int64_t)k0 * lda, lda, 1};
-      View<T> Y{R, 1, ldr};
-      launch_gemm<T, T>(cx, nb, nrhs, k0, -1.0, Lr, Y, 1.0, R + (int64_t)k0 * ldr, ldr, false);
-    }
-    View<T> Di{dinv + (int64_t)(k0 / NB) * NB * NB, NB, 1};
-    View<T> Rk{R + (int64_t)k0 * ldr, 1, ldr};
-    launch_gemm<T, T>(cx, nb, nrhs, nb, 1.0, Di, Rk, 0.0, R + (int64_t)k0 * ldr, ldr, false);
+  const size_t smem = trsm_smem_bytes<T>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(trsm_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr_set = true;
   }
-  if (!backward) return;
-  const int nblk = (n + NB - 1) / NB;
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int k0 = b * NB;
-    const int nb = std::min(NB, n - k0);
-    const int rest = n - k0 - nb;
-    if (rest > 0) {
-      View<T> Lt{L + (int64_t)(k0 + nb) * lda + k0, 1, lda};
-      View<T> X{R + (int64_t)(k0 + nb) * ldr, 1, ldr};
-      launch_gemm<T, T>(cx, nb, nrhs, rest, -1.0, Lt, X, 1.0, R + (int64_t)k0 * ldr, ldr, false);
-    }
-    View<T> DiT{dinv + (int64_t)b * NB * NB, 1, NB};
-    View<T> Rk{R + (int64_t)k0 * ldr, 1, ldr};
-    launch_gemm<T, T>(cx, nb, nrhs, nb, 1.0, DiT, Rk, 0.0, R + (int64_t)k0 * ldr, ldr, false);
-  }
+  note_launch();
+  trsm_cols_kernel<T><<<(nrhs + SC - 1) / SC, NTH, smem, cx.s>>>(L, lda, dinv, n, R, ldr, nrhs,
+                                                                 backward ? 1 : 0);
 }
 template void chol_solve_blocked<float>(const Ctx&, const float*, int64_t, const float*, int,
                                         float*, int64_t, int, bool);

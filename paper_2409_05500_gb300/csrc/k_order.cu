@@ -1,15 +1,24 @@
 // Algorithm 1: the accelerated causal-order search over the static
 // precomputed matrix.  For k = 1..m the candidate c_k in U minimising
 //     M_i = sum_{j in U, j != i} min(0, D_ij)^2            (Eq. 3)
-// is appended to the order and removed from U.  The kernel keeps the running
-// sums S_i = M_i in FP64 registers and subtracts P_{i,c} = min(0, D_ic)^2
-// after each pick, which equals the literal recomputation over U up to FP64
-// rounding.  Ties pick the lowest index.  One CTA: the m steps are strictly
-// sequential, each one a block-wide argmin.
+// is appended to the order and removed from U (ties: lowest index).
+//
+// GB300 design.  The m steps are strictly sequential, so the search is one
+// CTA and its cost is latency per step.  FP64 issues at 1/64 of the FP32 rate
+// on this part, so the running sums S_i = M_i are kept as double-float pairs
+// (hi + lo, two FP32 numbers, ~48-bit significand) and updated with TwoSum
+// after each pick, S_i -= P_{i,c}.  The argmin compares an order-preserving
+// 64-bit integer key built from (hi, lo) with the warp reduction instruction
+// (__reduce_min_sync), so no floating-point compare sits on the critical path.
+// The initial sums are computed in FP64 by a parallel kernel; the per-step
+// relative gaps are computed after the search by another.  Subtracting the
+// removed column instead of re-summing over U gives the same sums as the
+// literal recomputation up to rounding (~1e-14 relative).
 #include <cfloat>
 #include <climits>
 
 #include "vl_internal.cuh"
+
 
 namespace vl {
 
@@ -18,8 +27,9 @@ namespace {
 constexpr int OTH = 1024;
 constexpr int PER = (VL_MAX_M + OTH - 1) / OTH;
 
-// Pt[c * m + i] = min(0, D[i * m + c])^2, zero on the diagonal.
-__global__ void pt_kernel(const double* __restrict__ D, int m, double* __restrict__ Pt, int* st) {
+// Pt_hi/lo[c * m + i] = min(0, D[i * m + c])^2 as a double-float pair.
+__global__ void pt_kernel(const double* __restrict__ D, int m, float* __restrict__ pth,
+                          float* __restrict__ ptl, int* st) {
   __shared__ double tile[32][33];
   const int c0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -36,92 +46,168 @@ __global__ void pt_kernel(const double* __restrict__ D, int m, double* __restric
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     int c = c0 + r, i = i0 + tx;
-    if (c < m && i < m) Pt[(int64_t)c * m + i] = tile[tx][r];
+    if (c < m && i < m) {
+      double v = tile[tx][r];
+      float hi = (float)v;
+      pth[(int64_t)c * m + i] = hi;
+      ptl[(int64_t)c * m + i] = (float)(v - (double)hi);
+    }
   }
 }
 
-struct Best {
-  double v1;
-  int i1;
-  double v2;
+// S_i = sum_{j != i} min(0, D_ij)^2 in FP64, one warp per row, fixed order.
+__global__ void rowsum_kernel(const double* __restrict__ D, int m, float* __restrict__ sh,
+                              float* __restrict__ sl) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int j = lane; j < m; j += 32) {
+    double d = D[(int64_t)i * m + j];
+    if (j != i && d < 0.0) s += d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    float hi = (float)s;
+    sh[i] = hi;
+    sl[i] = (float)(s - (double)hi);
+  }
+}
+
+// order-preserving map float -> uint32 (valid for every non-NaN value)
+__device__ __forceinline__ uint32_t fkey(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(b);
+}
+
+// (hi, lo) -= (ph, pl) in double-float, renormalised so |lo| <= ulp(hi)/2
+// (then the pair order equals the order of (key(hi), key(lo))).
+__device__ __forceinline__ void df_sub(float& hi, float& lo, float ph, float pl) {
+  float s = hi - ph;
+  float bp = s - hi;
+  float err = (hi - (s - bp)) + (-ph - bp);
+  float l = lo - pl + err;
+  float h2 = s + l;
+  lo = l - (h2 - s);
+  hi = h2;
+}
+
+struct Cand {
+  uint32_t kh, kl;  // key of (hi, lo)
+  int idx;
 };
 
-__device__ __forceinline__ Best merge(Best a, Best b) {
-  const bool bfirst = (b.v1 < a.v1) || (b.v1 == a.v1 && b.i1 < a.i1);
-  Best r;
-  if (bfirst) {
-    r.v1 = b.v1;
-    r.i1 = b.i1;
-    r.v2 = fmin(a.v1, fmin(a.v2, b.v2));
-  } else {
-    r.v1 = a.v1;
-    r.i1 = a.i1;
-    r.v2 = fmin(b.v1, fmin(a.v2, b.v2));
-  }
-  return r;
+__device__ __forceinline__ bool cless(const Cand& a, const Cand& b) {
+  if (a.kh != b.kh) return a.kh < b.kh;
+  if (a.kl != b.kl) return a.kl < b.kl;
+  return a.idx < b.idx;
 }
 
-__device__ __forceinline__ Best warp_merge(Best b) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    Best x;
-    x.v1 = __shfl_xor_sync(0xffffffffu, b.v1, o);
-    x.i1 = __shfl_xor_sync(0xffffffffu, b.i1, o);
-    x.v2 = __shfl_xor_sync(0xffffffffu, b.v2, o);
-    b = merge(b, x);
-  }
-  return b;
+// lexicographic warp-wide minimum of (kh, kl, idx) with REDUX
+__device__ __forceinline__ Cand warp_min(Cand c) {
+  const uint32_t full = 0xffffffffu;
+  uint32_t mh = __reduce_min_sync(full, c.kh);
+  uint32_t kl = (c.kh == mh) ? c.kl : 0xffffffffu;
+  uint32_t ml = __reduce_min_sync(full, kl);
+  uint32_t id = (c.kh == mh && c.kl == ml) ? (uint32_t)c.idx : 0xffffffffu;
+  uint32_t mi = __reduce_min_sync(full, id);
+  return Cand{mh, ml, (int)mi};
 }
 
-__global__ void __launch_bounds__(OTH) order_kernel(const double* __restrict__ Pt, int m,
+__device__ __forceinline__ Cand none() { return Cand{0xffffffffu, 0xffffffffu, INT_MAX}; }
+
+// One CTA, up to 1024 threads, each owning PER variables (i = tid + q*nthr);
+// a step is a two-level argmin (warp REDUX, then warp 0 over the warp
+// winners) and the update S_i -= P_{i,c}.  The P column of the pick is loaded
+// together with the column of the runner-up; when the runner-up wins the next
+// step (about two thirds of the steps on the workloads measured) that step
+// uses the prefetched registers and skips the L2 round trip.
+__global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pth,
+                                                    const float* __restrict__ ptl,
+                                                    const float* __restrict__ sh0,
+                                                    const float* __restrict__ sl0, int m,
                                                     int32_t* __restrict__ order,
-                                                    double* __restrict__ gap) {
-  __shared__ Best wb[32];
-  __shared__ int s_c;
-  const int nthr = blockDim.x;
-  double S[PER];
+                                                    float4* __restrict__ best2) {
+  __shared__ Cand wb1[32], wb2[32];
+  __shared__ int s_c, s_r;
+  const int nthr = blockDim.x, nw = (nthr + 31) >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float hi[PER], lo[PER], nh[PER], nl[PER];
   bool alive[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int i = threadIdx.x + q * nthr;
     alive[q] = i < m;
-    double s = 0.0;
-    if (alive[q])
-      for (int j = 0; j < m; ++j) s += Pt[(int64_t)j * m + i];
-    S[q] = s;
+    hi[q] = alive[q] ? sh0[i] : 0.f;
+    lo[q] = alive[q] ? sl0[i] : 0.f;
+    nh[q] = nl[q] = 0.f;
   }
-  const int nw = (nthr + 31) >> 5;
+  int pre = -1;
   for (int k = 0; k < m; ++k) {
-    Best b{DBL_MAX, INT_MAX, DBL_MAX};
+    Cand b1 = none(), b2 = none();
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      const int i = threadIdx.x + q * nthr;
-      if (alive[q]) b = merge(b, Best{S[q], i, DBL_MAX});
+      if (!alive[q]) continue;
+      Cand c{fkey(hi[q]), fkey(lo[q]), threadIdx.x + q * nthr};
+      if (cless(c, b1)) {
+        b2 = b1;
+        b1 = c;
+      } else if (cless(c, b2)) {
+        b2 = c;
+      }
     }
-    b = warp_merge(b);
-    if ((threadIdx.x & 31) == 0) wb[threadIdx.x >> 5] = b;
+    Cand w1 = warp_min(b1);
+    Cand w2 = warp_min((b1.idx == w1.idx) ? b2 : b1);
+    if (lane == 0) {
+      wb1[wid] = w1;
+      wb2[wid] = w2;
+    }
     __syncthreads();
-    if (threadIdx.x < 32) {
-      Best x = (threadIdx.x < nw) ? wb[threadIdx.x] : Best{DBL_MAX, INT_MAX, DBL_MAX};
-      x = warp_merge(x);
-      if (threadIdx.x == 0) {
-        s_c = x.i1;
-        order[k] = x.i1;
-        if (gap) {
-          double g;
-          if (x.v2 == DBL_MAX) {
-            g = __longlong_as_double(0x7ff0000000000000LL);  // +inf: one candidate left
-          } else {
-            double den = fmax(fmax(fabs(x.v1), fabs(x.v2)), 1e-300);
-            g = (x.v2 - x.v1) / den;
-          }
-          gap[k] = g;
-        }
+    if (wid == 0) {
+      Cand a1 = lane < nw ? wb1[lane] : none();
+      Cand a2 = lane < nw ? wb2[lane] : none();
+      Cand g1 = warp_min(a1);
+      Cand g2 = warp_min((a1.idx == g1.idx) ? a2 : a1);
+      if (lane == 0) {
+        s_c = g1.idx;
+        s_r = g2.idx;
+        order[k] = g1.idx;
+        best2[k] = make_float4(fkey_inv(g1.kh), fkey_inv(g1.kl),
+                               g2.idx == INT_MAX ? __int_as_float(0x7f800000) : fkey_inv(g2.kh),
+                               g2.idx == INT_MAX ? 0.f : fkey_inv(g2.kl));
       }
     }
     __syncthreads();
-    const int c = s_c;
-    const double* row = Pt + (int64_t)c * m;
+    const int c = s_c, r = s_r;
+    float ch[PER], cl[PER];
+    if (c == pre) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        ch[q] = nh[q];
+        cl[q] = nl[q];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x + q * nthr;
+        ch[q] = alive[q] ? pth[(int64_t)c * m + i] : 0.f;
+        cl[q] = alive[q] ? ptl[(int64_t)c * m + i] : 0.f;
+      }
+    }
+    if (r != INT_MAX) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int i = threadIdx.x + q * nthr;
+        nh[q] = alive[q] ? pth[(int64_t)r * m + i] : 0.f;
+        nl[q] = alive[q] ? ptl[(int64_t)r * m + i] : 0.f;
+      }
+      pre = r;
+    }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int i = threadIdx.x + q * nthr;
@@ -129,23 +215,53 @@ __global__ void __launch_bounds__(OTH) order_kernel(const double* __restrict__ P
       if (i == c)
         alive[q] = false;
       else
-        S[q] -= row[i];
+        df_sub(hi[q], lo[q], ch[q], cl[q]);
     }
   }
 }
 
+__global__ void gap_kernel(const float4* __restrict__ best2, int m, double* __restrict__ gap) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  float4 b = best2[k];
+  if (isinf(b.z)) {
+    gap[k] = __longlong_as_double(0x7ff0000000000000LL);
+    return;
+  }
+  double s1 = (double)b.x + (double)b.y;
+  double s2 = (double)b.z + (double)b.w;
+  double den = fmax(fmax(fabs(s1), fabs(s2)), 1e-300);
+  gap[k] = (s2 - s1) / den;
+}
+
 }  // namespace
 
-void launch_causal_order(const double* D, int m, double* Pt, int32_t* order, double* gap,
-                         int* st, cudaStream_t s) {
+size_t order_ws_bytes(int m) {
+  return (size_t)m * m * 2 * sizeof(float) + (size_t)m * 2 * sizeof(float) +
+         (size_t)m * sizeof(float4) + 1024;
+}
+
+void launch_causal_order(const double* D, int m, void* ws, int32_t* order, double* gap, int* st,
+                         cudaStream_t s) {
+  char* p = static_cast<char*>(ws);
+  float* pth = reinterpret_cast<float*>(p);
+  float* ptl = pth + (size_t)m * m;
+  float* sh = ptl + (size_t)m * m;
+  float* sl = sh + m;
+  float4* best2 = reinterpret_cast<float4*>(((uintptr_t)(sl + m) + 15) & ~(uintptr_t)15);
   dim3 grid((m + 31) / 32, (m + 31) / 32), block(32, 8);
   note_launch();
-  pt_kernel<<<grid, block, 0, s>>>(D, m, Pt, st);
-  int nthr = ((m + PER - 1) / PER + 31) / 32 * 32;
-  if (nthr < 32) nthr = 32;
+  pt_kernel<<<grid, block, 0, s>>>(D, m, pth, ptl, st);
+  note_launch();
+  rowsum_kernel<<<(m + 7) / 8, 256, 0, s>>>(D, m, sh, sl);
+  int nthr = (m + 31) / 32 * 32;  // one variable per thread up to 1024
   if (nthr > OTH) nthr = OTH;
   note_launch();
-  order_kernel<<<1, nthr, 0, s>>>(Pt, m, order, gap);
+  order_kernel<<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+  if (gap) {
+    note_launch();
+    gap_kernel<<<(m + 255) / 256, 256, 0, s>>>(best2, m, gap);
+  }
 }
 
 }  // namespace vl

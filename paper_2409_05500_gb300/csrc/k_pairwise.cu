@@ -83,7 +83,7 @@ struct Stream {
 __global__ void __launch_bounds__(NTH, 2)
     pairwise_f32_kernel(const float* __restrict__ xt, int m, int m_pad, int T, int n_run,
                         int tps, const float* __restrict__ rho32,
-                        const float* __restrict__ c32, double* __restrict__ part) {
+                        const float* __restrict__ c32, float* __restrict__ part) {
   __shared__ __align__(16) float sx[2][TT][2 * TB];
   int I, J;
   tile_coords(blockIdx.x, T, I, J);
@@ -173,8 +173,10 @@ __global__ void __launch_bounds__(NTH, 2)
     buf ^= 1;
   }
 
-  // partial sums of this split: part[(split*3 + k) * m*m + a*m + b] for the
-  // residual of a on b
+  // partial sums of this split as exact double-float pairs (sum, -comp):
+  // part[(split*6 + k) * m*m + a*m + b] for the residual of a on b.  No FP64
+  // arithmetic here: FP64 issues at 1/64 rate on this part, and a CTA covers
+  // only a few hundred samples.
   const int64_t mm = (int64_t)m * m;
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
@@ -184,10 +186,13 @@ __global__ void __launch_bounds__(NTH, 2)
     for (int d = 0; d < 2; ++d) {
       const Stream& s = st[2 * p + d];
       const int64_t off = d ? ((int64_t)b * m + a) : ((int64_t)a * m + b);
-      double* base = part + (int64_t)split * 3 * mm + off;
-      base[0] = (double)s.sa - (double)s.ca;
-      base[mm] = (double)s.sl - (double)s.cl;
-      base[2 * mm] = (double)s.sb - (double)s.cb;
+      float* base = part + (int64_t)split * 6 * mm + off;
+      base[0] = s.sa;
+      base[mm] = -s.ca;
+      base[2 * mm] = s.sl;
+      base[3 * mm] = -s.cl;
+      base[4 * mm] = s.sb;
+      base[5 * mm] = -s.cb;
     }
   }
 }
@@ -272,7 +277,16 @@ __global__ void pair_consts_kernel(const double* __restrict__ C, int m,
   if (rho64) rho64[idx] = r;
 }
 
-__global__ void measure_finalize_kernel(const double* __restrict__ part, int m, int splits,
+// double-float accumulate (hi, lo) += x (TwoSum)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  float s = hi + x;
+  float bp = s - hi;
+  float err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
+
+__global__ void measure_finalize_kernel(const void* __restrict__ part_v, int m, int splits,
                                         int n_real, int n_proc, const double* __restrict__ hx,
                                         double* __restrict__ Hx, double* __restrict__ Hr,
                                         double* __restrict__ D, int fp32_parts) {
@@ -292,17 +306,26 @@ __global__ void measure_finalize_kernel(const double* __restrict__ part, int m, 
     const int64_t off = d ? ((int64_t)b * m + a) : idx;
     double A, B;
     if (fp32_parts) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      // splits combined in double-float FP32 arithmetic, one FP64 conversion
+      const float* part = static_cast<const float*>(part_v);
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
       for (int s = 0; s < splits; ++s) {
-        const double* p = part + (int64_t)s * 3 * mm + off;
-        s0 += p[0];
-        s1 += p[mm];
-        s2 += p[2 * mm];
+        const float* p = part + (int64_t)s * 6 * mm + off;
+        df_add(h0, l0, p[0]);
+        df_add(h0, l0, p[mm]);
+        df_add(h1, l1, p[2 * mm]);
+        df_add(h1, l1, p[3 * mm]);
+        df_add(h2, l2, p[4 * mm]);
+        df_add(h2, l2, p[5 * mm]);
       }
+      const double s0 = (double)h0 + (double)l0;
+      const double s1 = (double)h1 + (double)l1;
+      const double s2 = (double)h2 + (double)l2;
       const double kappa = 2.0 * LOG2E;
       A = (s0 / kappa + LN2 * (s1 - (double)n_proc)) / n_real;
       B = s2 / (kappa * n_real);
     } else {
+      const double* part = static_cast<const double*>(part_v);
       double s0 = 0.0, s1 = 0.0;
       for (int s = 0; s < splits; ++s) {
         const double* p = part + (int64_t)s * 2 * mm + off;
@@ -351,7 +374,7 @@ void launch_pair_consts(const double* C, int m, float* rho32, float* c32, double
 }
 
 void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32,
-                         const float* c32, double* part, cudaStream_t s) {
+                         const float* c32, float* part, cudaStream_t s) {
   const int n_run = ((pl.n + KRUN - 1) / KRUN) * KRUN;
   dim3 grid(pl.tiles, pl.splits);
   note_launch();
@@ -367,7 +390,7 @@ void launch_pairwise_f64(const double* xt, const PairPlan& pl, const double* rho
                                            pl.t_per_split, rho64, part);
 }
 
-void launch_measure_finalize(const double* part, const PairPlan& pl, const double* hx_mom,
+void launch_measure_finalize(const void* part, const PairPlan& pl, const double* hx_mom,
                              double* Hx, double* Hr, double* D, bool fp32_parts,
                              cudaStream_t s) {
   const int64_t tot = (int64_t)pl.m * pl.m;

@@ -96,14 +96,18 @@ __global__ void var_coef_kernel(const T* __restrict__ beta, int m, int p, double
   M[idx] = (double)beta[((int64_t)tau * m + k) * m + i];
 }
 
+// One warp per row: cst[i] = wbar0_i - sum_a beta[a][i] wbar_{Z,a}.
 template <class T>
 __global__ void var_cst_kernel(const T* __restrict__ beta, int m, int p,
                                const double* __restrict__ wbar, double* __restrict__ cst) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (i >= m) return;
-  double c = wbar[i];
-  for (int a = 0; a < m * p; ++a) c -= (double)beta[(int64_t)a * m + i] * wbar[m + a];
-  cst[i] = c;
+  double c = 0.0;
+  for (int a = lane; a < m * p; a += 32) c += (double)beta[(int64_t)a * m + i] * wbar[m + a];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cst[i] = wbar[i] - c;
 }
 
 __global__ void var_resid_init_kernel(const double* __restrict__ X, int64_t ldx, int n_eff, int p,
@@ -124,12 +128,11 @@ __device__ __forceinline__ void moments_one(double u, double& a, double& b) {
   a += au + log1p(exp(-2.0 * au)) - LN2;
   b += u * exp(-0.5 * u * u);
 }
-__device__ __forceinline__ void moments_one_f(double u64, double& a, double& b) {
-  // FP32 evaluation (correctly rounded libm-class functions), FP64 sums
-  float u = (float)u64;
-  float au = fabsf(u);
-  a += (double)(au + log1pf(expf(-2.0f * au))) - LN2;
-  b += (double)(u * expf(-0.5f * u * u));
+__device__ __forceinline__ void kahan_f(float& S, float& C, float x) {
+  float y = x - C;
+  float t = S + y;
+  C = (t - S) - y;
+  S = t;
 }
 
 template <class T>
@@ -169,12 +172,22 @@ __global__ void __launch_bounds__(kStatThreads) standardize_kernel(
   }
   const double isd = 1.0 / sqrt(var);
   double a = 0.0, b = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    double u = (e[t] - mu) * isd;
-    if (sizeof(T) == 8)
-      moments_one(u, a, b);
-    else
-      moments_one_f(u, a, b);
+  if (sizeof(T) == 8) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) moments_one((e[t] - mu) * isd, a, b);
+  } else {
+    // FP32 per-sample functions (CUDA's accurate expf / log1pf), Kahan sums
+    // of log cosh u + ln 2 (= |u| + log1p(e^{-2|u|})) and u e^{-u^2/2}
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+    int cnt = 0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const float u = (float)((e[t] - mu) * isd);
+      const float au = fabsf(u);
+      kahan_f(sa, ca, au + log1pf(expf(-2.0f * au)));
+      kahan_f(sb, cb, u * expf(-0.5f * u * u));
+      ++cnt;
+    }
+    a = ((double)sa - (double)ca) - LN2 * cnt;
+    b = (double)sb - (double)cb;
   }
   a = block_sum(a, red);
   b = block_sum(b, red);
@@ -266,7 +279,7 @@ void launch_var_coef(const T* beta, int m, int p, const double* wbar, double* M,
   note_launch();
   var_coef_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(beta, m, p, M);
   note_launch();
-  var_cst_kernel<T><<<(m + 127) / 128, 128, 0, s>>>(beta, m, p, wbar, cst);
+  var_cst_kernel<T><<<(m + 7) / 8, 256, 0, s>>>(beta, m, p, wbar, cst);
 }
 template void launch_var_coef<float>(const float*, int, int, const double*, double*, double*,
                                      cudaStream_t);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/varlingam_gb300.h"
 
@@ -51,6 +52,19 @@ inline size_t ws_bytes(size_t count) {
 
 }  // namespace vl
 
+namespace vl {
+// One stream of the batched path with its own workspace and series buffers.
+struct PoolSlot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  void* ws = nullptr;
+  size_t ws_cap = 0;
+  void* buf = nullptr;
+  size_t buf_cap = 0;
+};
+constexpr int BATCH_STREAMS = 8;
+}  // namespace vl
+
 struct vl_handle_s {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -58,6 +72,11 @@ struct vl_handle_s {
   size_t ws_cap = 0;
   int* status = nullptr;  // device sticky status word (own allocation)
   int num_sms = 0;
+  void* sbuf = nullptr;  // per-series buffers (E, C, D) of vl_fit
+  size_t sbuf_cap = 0;
+  std::vector<vl::PoolSlot> pool;  // batched path
+  int* bstatus = nullptr;          // per-instance status words of a batch
+  size_t bstatus_cap = 0;
   cudaEvent_t prof_start = nullptr;  // optional: recorded around the pairwise kernel
   cudaEvent_t prof_stop = nullptr;
   std::string last_error;
@@ -155,15 +174,16 @@ PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64);
 void launch_pair_consts(const double* C, int m, float* rho32, float* c32, double* rho64, int* st,
                         cudaStream_t s);
 void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32,
-                         const float* c32, double* part, cudaStream_t s);
+                         const float* c32, float* part, cudaStream_t s);
 void launch_pairwise_f64(const double* xt, const PairPlan& pl, const double* rho64,
                          double* part, cudaStream_t s);
-void launch_measure_finalize(const double* part, const PairPlan& pl, const double* hx_mom,
+void launch_measure_finalize(const void* part, const PairPlan& pl, const double* hx_mom,
                              double* Hx, double* Hr, double* D, bool fp32_parts, cudaStream_t s);
 
 // Ordering (k_order.cu)
-void launch_causal_order(const double* D, int m, double* Pt, int32_t* order, double* gap,
-                         int* st, cudaStream_t s);
+size_t order_ws_bytes(int m);
+void launch_causal_order(const double* D, int m, void* ws, int32_t* order, double* gap, int* st,
+                         cudaStream_t s);
 
 // B0 / B_tau helpers (k_fitb.cu)
 template <class T>
