@@ -134,6 +134,31 @@ vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, 
 vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, double* gap);
 
 /*
+ * Allocation-free variant of vl_causal_order (same search, same results).
+ * This entry point has no counterpart in the paper; it exists for callers that
+ * cannot allocate device memory when they need the ordering: code running
+ * under CUDA stream capture (where cudaMalloc is not allowed), frameworks
+ * that own all device memory through their own allocator, and latency-bound
+ * loops where an allocation would stall the device.  It needs no handle and
+ * allocates nothing: its scratch is a fixed device array inside the library
+ * (about 2.1 MB, held on every GPU that loads the library until the process
+ * exits), so it accepts 1 <= m <= VL_NOALLOC_MAX_M and returns
+ * VL_ERR_UNSUPPORTED above that.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress); make this first call before any stream capture.
+ *  - All calls share the one array: calls that may overlap on the GPU (on
+ *    different streams without ordering between them) race.  A call needs no
+ *    zeroed scratch: it writes every scratch element before reading it.
+ *  - Work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
+ *    stream) and the call returns without waiting.  Only host-side argument
+ *    errors are reported; non-finite entries of D are not detected here (use
+ *    vl_causal_order when D is not known to be finite).
+ */
+#define VL_NOALLOC_MAX_M 512
+vl_status vl_causal_order_noalloc(void* cuda_stream, const double* D, int m, int32_t* order,
+                                  double* gap);
+
+/*
  * B0 and B_tau from a causal order (Sec. 4: the instantaneous matrix of
  * VarLiNGAM): row order[k] of B0 holds the least-squares coefficients of
  * e_{order[k]} on e_{order[0..k-1]}; then B_tau = (I - B0) M_tau.

@@ -35,7 +35,8 @@ PRECISIONS = {"fp64": VL_PREC_FP64, "mixed": VL_PREC_MIXED}
 
 EXPORTED = ("vl_create", "vl_destroy", "vl_set_stream", "vl_reserve", "vl_sync",
             "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_fit", "vl_var_fit",
-            "vl_pairwise_measure", "vl_causal_order", "vl_fit_b", "vl_fit_batched")
+            "vl_pairwise_measure", "vl_causal_order", "vl_causal_order_noalloc", "vl_fit_b",
+            "vl_fit_batched")
 
 
 class VLError(RuntimeError):
@@ -67,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "vl_var_fit": [P, P, I64, I, I, I, I, P, P],
         "vl_pairwise_measure": [P, P, I64, I, I, I, P, P, P],
         "vl_causal_order": [P, P, I, P, P],
+        "vl_causal_order_noalloc": [P, P, I, P, P],
         "vl_fit_b": [P, P, I64, I, I, P, P, I, I, P, P],
         "vl_fit_batched": [P, ctypes.POINTER(vl_instance), I, I, ctypes.POINTER(I)],
         "vl_fit": [P, P, I64, I, I, I, I, P, P, P, P, P],
@@ -170,6 +172,18 @@ def vl_causal_order(h: Handle, D: torch.Tensor, order: torch.Tensor,
                     gap: Optional[torch.Tensor] = None) -> None:
     m = D.shape[0]
     h.check(_lib.vl_causal_order(h.h, _ptr(D), m, _ptr(order), _ptr(gap)), "vl_causal_order")
+
+
+def vl_causal_order_noalloc(D: torch.Tensor, order: torch.Tensor,
+                            gap: Optional[torch.Tensor] = None,
+                            stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Allocation-free ordering on `stream` (default: the current stream);
+    m <= 512.  See include/varlingam_gb300.h for its rules."""
+    st = stream if stream is not None else torch.cuda.current_stream()
+    code = _lib.vl_causal_order_noalloc(ctypes.c_void_p(st.cuda_stream), _ptr(D), D.shape[0],
+                                        _ptr(order), _ptr(gap))
+    if code != VL_OK:
+        raise VLError(code, "vl_causal_order_noalloc")
 
 
 def vl_fit_b(h: Handle, E: torch.Tensor, order: torch.Tensor, M: Optional[torch.Tensor],

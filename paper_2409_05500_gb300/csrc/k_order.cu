@@ -16,6 +16,7 @@
 // literal recomputation up to rounding (~1e-14 relative).
 #include <cfloat>
 #include <climits>
+#include <mutex>
 
 #include "vl_internal.cuh"
 
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pt
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       if (!alive[q]) continue;
-      Cand c{fkey(hi[q]), fkey(lo[q]), threadIdx.x + q * nthr};
+      Cand c{fkey(hi[q]), fkey(lo[q]), (int)threadIdx.x + q * nthr};
       if (cless(c, b1)) {
         b2 = b1;
         b1 = c;
@@ -265,3 +266,56 @@ void launch_causal_order(const double* D, int m, void* ws, int32_t* order, doubl
 }
 
 }  // namespace vl
+
+// ------------------------------------------------------------------------
+// Allocation-free variant of the search, for callers that must not allocate
+// device memory after start-up.  Its scratch is this file-scope array; every
+// GPU that loads the library holds it until the process exits.
+namespace vl {
+namespace {
+
+constexpr size_t kNoallocBytes =
+    (size_t)VL_NOALLOC_MAX_M * VL_NOALLOC_MAX_M * 2 * sizeof(float) +
+    (size_t)VL_NOALLOC_MAX_M * 2 * sizeof(float) + (size_t)VL_NOALLOC_MAX_M * sizeof(float4) +
+    1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+}  // namespace vl
+
+extern "C" vl_status vl_causal_order_noalloc(void* cuda_stream, const double* D, int m,
+                                             int32_t* order, double* gap) {
+  using namespace vl;
+  if (!D || !order) return VL_ERR_ARG;
+  if (m < 1) return VL_ERR_SHAPE;
+  if (m > VL_NOALLOC_MAX_M) return VL_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return VL_ERR_CUDA;
+  }
+  void* scratch;
+  {
+    // first call on this device: resolve the array's device address (host
+    // code cannot use the symbol itself: on the host it names a stand-in)
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return VL_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (order_ws_bytes(m) > kNoallocBytes) return VL_ERR_UNSUPPORTED;
+  launch_causal_order(D, m, scratch, order, gap, nullptr, static_cast<cudaStream_t>(cuda_stream));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VL_OK : VL_ERR_CUDA;
+}
