@@ -14,7 +14,7 @@
 //     sa  += |w|
 //     g    = ex2(-w^2 / (8 log2 e))     = e^{-u^2/2}   (MUFU)
 //     sb  += w g
-// Every KRUN samples the run sums are Kahan-added into FP32 (sum, comp)
+// Every KRUN = 16 samples the run sums are Kahan-added into FP32 (sum, comp)
 // pairs and log2(prod) (one MUFU lg2 per run) is Kahan-added as well, so
 // sum_t ln(1 + y_t) = ln 2 * sum_runs log2(prod_run).  The split partials are
 // written as FP64 and combined in a fixed order by measure_finalize.
@@ -32,8 +32,8 @@ namespace vl {
 namespace {
 
 constexpr int TB = 32;        // variables per tile side
-constexpr int TT = 64;        // samples per shared-memory stage
-constexpr int KRUN = 8;       // samples per product/Kahan run
+constexpr int TT = 128;       // samples per shared-memory stage
+constexpr int KRUN = 16;      // samples per product/Kahan run (product <= 2^16)
 constexpr int NTH = 256;      // threads: 16 x 16, each a 2 x 2 pair micro-tile
 constexpr float KAPPA = 2.8853900817779268f;       // 2 log2(e)
 constexpr float GAUSS_K = -0.08664339756999316f;   // -1 / (8 log2 e)
@@ -80,18 +80,49 @@ struct Stream {
   float sa, ca, sb, cb, sl, cl;
 };
 
+// Thread -> 2 x 2 pair micro-tile (ti, tj) of tile (I, J), enumerating only
+// micro-tiles holding at least one pair i < j < m; returns false for threads
+// beyond that count.
+__device__ __forceinline__ bool micro_tile(int s, int I, int J, int m, int& ti, int& tj) {
+  const int lim = min(16, (m - J * TB + 1) / 2);  // micro-columns with some j < m
+  if (I < J) {
+    ti = s / lim;
+    tj = s % lim;
+    if (ti < 16) return true;
+  } else {
+    // upper triangle ti <= tj < lim, row by row
+    for (int r = 0; r < lim; ++r) {
+      const int len = lim - r;
+      if (s < len) {
+        ti = r;
+        tj = r + s;
+        return true;
+      }
+      s -= len;
+    }
+  }
+  ti = 0;
+  tj = 0;
+  return false;
+}
+
 __global__ void __launch_bounds__(NTH, 2)
     pairwise_f32_kernel(const float* __restrict__ xt, int m, int m_pad, int T, int n_run,
                         int tps, const float* __restrict__ rho32,
                         const float* __restrict__ c32, float* __restrict__ part) {
-  __shared__ __align__(16) float sx[2][TT][2 * TB];
+  extern __shared__ __align__(16) float pw_smem[];
+  float(*sx)[TT][2 * TB] = reinterpret_cast<float(*)[TT][2 * TB]>(pw_smem);  // [2][TT][64]
   int I, J;
   tile_coords(blockIdx.x, T, I, J);
   const int split = blockIdx.y;
   const int t0 = split * tps;
   const int t1 = min(n_run, t0 + tps);
 
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  // Valid 2 x 2 pair micro-tiles first: on a diagonal tile only ti <= tj,
+  // on the last tile column only j < m; threads past the valid count (whole
+  // warps, at the end) skip the arithmetic and only help stage the samples.
+  int ti, tj;
+  const bool active = micro_tile(threadIdx.x, I, J, m, ti, tj);
   const int li = 2 * ti, lj = 2 * tj;
   const int gi0 = I * TB + li, gj0 = J * TB + lj;
 
@@ -100,7 +131,7 @@ __global__ void __launch_bounds__(NTH, 2)
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     const int a = gi0 + (p >> 1), b = gj0 + (p & 1);
-    valid[p] = (a < b) && (b < m);
+    valid[p] = active && (a < b) && (b < m);
     rho[p] = valid[p] ? rho32[(int64_t)a * m + b] : 0.f;
     cc[p] = valid[p] ? c32[(int64_t)a * m + b] : KAPPA;
   }
@@ -132,7 +163,7 @@ __global__ void __launch_bounds__(NTH, 2)
       cp_async_wait<0>();
     }
     __syncthreads();
-    for (int r0 = 0; r0 < rows; r0 += KRUN) {
+    for (int r0 = 0; active && r0 < rows; r0 += KRUN) {
       float ra[8], rb[8], pr[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -353,10 +384,24 @@ PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64) {
   const int Tside = pl.m_pad / TB;
   pl.tiles = Tside * (Tside + 1) / 2;
   const int n_run = ((n + KRUN - 1) / KRUN) * KRUN;
-  // about four waves of 2 CTAs per SM, each split at least 2 stages long
-  int want = std::max(1, (8 * num_sms + pl.tiles - 1) / pl.tiles);
-  int max_split = std::max(1, n_run / (2 * TT));
-  int splits = std::min(want, max_split);
+  // Split the samples so that the CTA count fills whole waves of 2 CTAs per
+  // SM (about 3-6 waves), each split at least 2 stages long.
+  const int slots = 2 * num_sms;
+  const int max_split = std::max(1, n_run / (2 * TT));
+  int splits = 1;
+  double best = -1.0;
+  for (int sp = 1; sp <= max_split; ++sp) {
+    const long ctas = (long)pl.tiles * sp;
+    const long waves = (ctas + slots - 1) / slots;
+    if (waves > 8) break;
+    const double eff = (double)ctas / (double)(waves * slots);
+    // prefer full waves; among equals, at least 3 waves for load balance
+    const double score = eff - (waves < 3 ? 0.05 * (3 - waves) : 0.0);
+    if (score > best + 1e-9) {
+      best = score;
+      splits = sp;
+    }
+  }
   if (fp64) splits = std::min(std::max(1, (4 * num_sms + pl.tiles - 1) / pl.tiles), n);
   int tps = (n_run + splits - 1) / splits;
   tps = ((tps + KRUN - 1) / KRUN) * KRUN;
@@ -377,9 +422,16 @@ void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32
                          const float* c32, float* part, cudaStream_t s) {
   const int n_run = ((pl.n + KRUN - 1) / KRUN) * KRUN;
   dim3 grid(pl.tiles, pl.splits);
+  const size_t smem = sizeof(float) * 2 * TT * 2 * TB;  // two stages of TT x 64 samples
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(pairwise_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr_set = true;
+  }
   note_launch();
-  pairwise_f32_kernel<<<grid, NTH, 0, s>>>(xt, pl.m, pl.m_pad, pl.m_pad / TB, n_run,
-                                           pl.t_per_split, rho32, c32, part);
+  pairwise_f32_kernel<<<grid, NTH, smem, s>>>(xt, pl.m, pl.m_pad, pl.m_pad / TB, n_run,
+                                              pl.t_per_split, rho32, c32, part);
 }
 
 void launch_pairwise_f64(const double* xt, const PairPlan& pl, const double* rho64,

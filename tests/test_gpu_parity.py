@@ -11,7 +11,9 @@ Tolerances (written here, used everywhere below):
                oracle's predecessor regression on that same order)
   M            1e-5 absolute (mixed) / 1e-9 (FP64)
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -56,8 +58,21 @@ def _measure_gpu(vl, h, E, prec):
     return Hx.cpu().numpy(), Hr.cpu().numpy(), D.cpu().numpy()
 
 
-def _check_measure(ref, Hx, Hr, D):
+def _report(key, **vals):
+    """With VL_REPORT_DIR set, append the measured errors (for the record)."""
+    out = os.environ.get("VL_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "parity_errors.jsonl"), "a") as f:
+            f.write(json.dumps({"case": key, **{k: float(v) for k, v in vals.items()}}) + "\n")
+
+
+def _check_measure(ref, Hx, Hr, D, key="measure"):
     dmax = np.abs(ref["D"]).max()
+    off = ~np.eye(D.shape[0], dtype=bool)
+    _report(key, d_rel=np.abs(D - ref["D"]).max() / dmax,
+            hx=np.max(np.abs(Hx - ref["Ex"]) / np.maximum(np.abs(ref["Ex"]), oracle.H_GAUSS)),
+            hr=np.max((np.abs(Hr - ref["Er"]) / np.maximum(np.abs(ref["Er"]), oracle.H_GAUSS))[off]))
     assert np.abs(D - ref["D"]).max() <= D_REL * dmax, np.abs(D - ref["D"]).max() / dmax
     assert np.allclose(D, -D.T, atol=1e-15 + 1e-12 * dmax)
     scale_x = np.maximum(np.abs(ref["Ex"]), oracle.H_GAUSS)
@@ -78,7 +93,7 @@ def test_pairwise_measure_small(vl, h, prec, m, n, seed):
     E[1:] += 0.5 * E[:-1]
     ref = _oracle_measure(("small", m, n, seed), E)
     Hx, Hr, D = _measure_gpu(vl, h, E, prec)
-    _check_measure(ref, Hx, Hr, D)
+    _check_measure(ref, Hx, Hr, D, key=f"small m={m} n={n} {prec}")
 
 
 @pytest.mark.parametrize("sizes", [(2, 5, 31, 64, 97), (300,), (700,), (1100,)])
@@ -127,14 +142,19 @@ def _ref_pipeline(key, inst):
     return _ref_cache[key]
 
 
-def _check_pipeline(ref, out, prec, p):
+def _check_pipeline(ref, out, prec, p, key="pipeline"):
     M = out["M"].cpu().numpy()
     assert np.abs(M - ref["M"]).max() <= (1e-5 if prec == "mixed" else 1e-9)
     E = out["E"].cpu().numpy()
     assert np.abs(E - ref["E"]).max() <= (1e-5 if prec == "mixed" else 1e-9) * np.abs(ref["E"]).max()
-    _check_measure(ref, out["Hx"].cpu().numpy(), out["Hr"].cpu().numpy(), out["D"].cpu().numpy())
+    _check_measure(ref, out["Hx"].cpu().numpy(), out["Hr"].cpu().numpy(), out["D"].cpu().numpy(),
+                   key=key)
     order = out["order"].cpu().numpy()
     ok, ties, bad = oracle.order_gap_ok(order, ref["D"], GAP)
+    B0_ref_o = oracle.b0_ols(ref["E"], order)
+    _report(key + " order/B", near_ties=ties, identical=float(np.array_equal(order, ref["order"])),
+            m_err=np.abs(M - ref["M"]).max(),
+            b0_err=np.abs(out["B0"].cpu().numpy() - B0_ref_o).max())
     assert ok, f"order differs beyond the near-tie rule at steps {bad}"
     B0_ref = oracle.b0_ols(ref["E"], order)
     assert np.abs(out["B0"].cpu().numpy() - B0_ref).max() <= B_ABS
@@ -148,7 +168,7 @@ def test_pipeline_small_workloads(vl, h, prec, name):
     inst = synth.make_config(name)
     ref = _ref_pipeline(name, inst)
     out = _fit_steps(vl, h, inst, prec)
-    _check_pipeline(ref, out, prec, inst.p)
+    _check_pipeline(ref, out, prec, inst.p, key=f"{name} {prec}")
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
@@ -156,7 +176,7 @@ def test_pipeline_server_workload(vl, h, prec):
     inst = synth.make_config("server")  # m=120, n=10000, p=3
     ref = _ref_pipeline("server", inst)
     out = _fit_steps(vl, h, inst, prec)
-    _check_pipeline(ref, out, prec, inst.p)
+    _check_pipeline(ref, out, prec, inst.p, key=f"server {prec}")
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
@@ -164,7 +184,7 @@ def test_pipeline_finance_workload(vl, h, prec):
     inst = synth.make_config("finance")  # m=400, n=2500, p=1
     ref = _ref_pipeline("finance", inst)
     out = _fit_steps(vl, h, inst, prec)
-    _check_pipeline(ref, out, prec, inst.p)
+    _check_pipeline(ref, out, prec, inst.p, key=f"finance {prec}")
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
