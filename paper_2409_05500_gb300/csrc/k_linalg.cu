@@ -37,7 +37,8 @@ __device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 // consecutive threads read consecutive k of a row, otherwise consecutive rows.
 template <class T, int BM>
 struct StageLoader {
-  static constexpr int PER = BM * KC / NTH;
+  static constexpr int TOT = BM * KC;
+  static constexpr int PER = (TOT + NTH - 1) / NTH;  // the last slot may be partial
   T v[PER];
   __device__ __forceinline__ static void slot(int idx, int ks, int& r, int& k) {
     if (ks == 1) {
@@ -51,8 +52,10 @@ struct StageLoader {
   __device__ __forceinline__ void load(const View<T>& w, int r0, int rows, int k0, int kmax) {
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
+      const int idx = threadIdx.x + e * NTH;
+      if (TOT % NTH != 0 && idx >= TOT) break;
       int r, k;
-      slot(threadIdx.x + e * NTH, w.ks, r, k);
+      slot(idx, w.ks, r, k);
       const int gr = r0 + r, gk = k0 + k;
       v[e] = (gr < rows && gk < kmax) ? w.base[(int64_t)gr * w.rs + (int64_t)gk * w.ks] : T(0);
     }
@@ -60,8 +63,10 @@ struct StageLoader {
   __device__ __forceinline__ void store(T* sm, int ks) const {  // sm[k * (BM + 4) + r]
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
+      const int idx = threadIdx.x + e * NTH;
+      if (TOT % NTH != 0 && idx >= TOT) break;
       int r, k;
-      slot(threadIdx.x + e * NTH, ks, r, k);
+      slot(idx, ks, r, k);
       sm[k * (BM + 4) + r] = v[e];
     }
   }
@@ -185,9 +190,15 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, int kchu
       if (r >= M || c >= N) continue;
       if (mode == 1 && c > r) continue;
       if (mode == 2 && c < r) continue;
-      if constexpr (!SPLIT && sizeof(TC) == 4 && sizeof(T) == 4) {
-        // all-FP32 epilogue: FP64 conversions run at 1/64 rate on this part
-        if (!part) {
+      if constexpr (!SPLIT && sizeof(T) == 4) {
+        // all-FP32 epilogue (FP64 conversions run at 1/64 rate on this part):
+        // split-K slices leave FP32 partials, reduced by splitk_reduce_f32
+        if (part) {
+          reinterpret_cast<float*>(part)[((int64_t)blockIdx.z * M + r) * N + c] =
+              (float)alpha * acc[x][y];
+          continue;
+        }
+        if constexpr (sizeof(TC) == 4) {
           float v = (float)alpha * acc[x][y];
           if (beta != 0.0) v = fmaf((float)beta, C[(int64_t)r * ldc + c], v);
           C[(int64_t)r * ldc + c] = v;
@@ -209,6 +220,33 @@ __global__ void __launch_bounds__(NTH) gemm_kernel(int M, int N, int K, int kchu
         if (mode == 2 && c != r) C[(int64_t)c * ldc + r] = (TC)v;
       }
     }
+}
+
+// FP32 partials of the plain FP32 GEMM: summed as a double-float pair, one
+// conversion per output.
+template <class TC>
+__global__ void splitk_reduce_f32_kernel(const float* __restrict__ part, int ksplit, int M,
+                                         int N, double beta, TC* __restrict__ C, int64_t ldc,
+                                         int mode) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)M * N) return;
+  int r = (int)(idx / N), c = (int)(idx % N);
+  if (mode == 1 && c > r) return;
+  if (mode == 2 && c < r) return;
+  float hi = 0.f, lo = 0.f;
+  for (int z = 0; z < ksplit; ++z) two_sum_acc(hi, lo, part[((int64_t)z * M + r) * N + c]);
+  TC v;
+  if constexpr (sizeof(TC) == 4) {
+    float f = hi + lo;
+    if (beta != 0.0) f = fmaf((float)beta, C[(int64_t)r * ldc + c], f);
+    v = f;
+  } else {
+    double d = (double)hi + (double)lo;
+    if (beta != 0.0) d += beta * (double)C[(int64_t)r * ldc + c];
+    v = d;
+  }
+  C[(int64_t)r * ldc + c] = v;
+  if (mode == 2 && c != r) C[(int64_t)c * ldc + r] = v;
 }
 
 template <class TC>
@@ -345,6 +383,189 @@ __global__ void __launch_bounds__(NTH) chol_diag_kernel(T* __restrict__ A, int64
     if (r < nb && c <= r) A[(int64_t)r * lda + c] = L[r][c];
     dinv[idx] = Li[r][c];
   }
+}
+
+// ---- Whole Cholesky factorisation in one CTA (FP32, n <= SINGLE_MAX).
+// 32-wide blocks; for each block column k0:
+//  1. warp 0 factors the 32 x 32 diagonal block in registers (lane r holds
+//     row r; the pivot column travels by shuffles) and inverts it;
+//  2. all warps form the panel L[i, k0:k0+32] = A[i, k0:k0+32] Linv^T for the
+//     rows below, kept in shared memory and written back;
+//  3. all warps update the trailing lower triangle in 32 x 32 tiles,
+//     A[i, j] -= sum_q P[i, q] P[j, q] (read-modify-write, L2 resident).
+// Finally the inverses of consecutive 32-blocks are combined into the 64 x 64
+// diagonal-block inverses the blocked solves use:
+//     [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}].
+constexpr int SB = 32;
+constexpr int SBP = SB + 4;  // panel row stride in shared memory (16-byte aligned rows)
+constexpr int SINGLE_MAX = 512;
+constexpr int STH = 512;
+
+__global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A, int64_t lda,
+                                                          int n, float* __restrict__ dinv,
+                                                          const double* __restrict__ diag0,
+                                                          float rel_tol, int* st) {
+  extern __shared__ __align__(16) float cs_smem[];
+  const int nblk = (n + SB - 1) / SB;
+  float* P = cs_smem;                             // [n][SBP] panel
+  float* Li = P + (size_t)n * SBP;                // [nblk][SB][SB + 1] block inverses
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned full = 0xffffffffu;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int b = 0; b < nblk; ++b) {
+    const int k0 = b * SB;
+    const int nb = min(SB, n - k0);
+    float* Lib = Li + (size_t)b * SB * (SB + 1);
+    if (warp == 0) {
+      float a[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        float v = (c == lane) ? 1.f : 0.f;  // identity padding
+        if (lane < nb && c < nb && c <= lane) v = A[(int64_t)(k0 + lane) * lda + k0 + c];
+        a[c] = v;
+      }
+      const float thr = lane < nb ? (float)(rel_tol * diag0[k0 + lane]) : 0.f;
+      bool lbad = false;
+#pragma unroll
+      for (int j = 0; j < SB; ++j) {
+        float d = __shfl_sync(full, a[j], j);
+        const float tj = __shfl_sync(full, thr, j);
+        if (!(d > tj)) {
+          lbad |= (j < nb);
+          d = 1.f;
+        }
+        const float ipiv = rsqrtf(d);  // one MUFU op: 1/sqrt(d), then 1/d and sqrt(d)
+        const float inv = ipiv * ipiv;
+        const float piv = d * ipiv;
+        const float lrj = a[j];  // (lane, j), not yet scaled
+#pragma unroll
+        for (int c = j + 1; c < SB; ++c) {
+          const float lcj = __shfl_sync(full, a[j], c);  // (c, j)
+          a[c] -= lrj * lcj * inv;
+        }
+        a[j] = (lane == j) ? piv : (lane > j ? lrj * ipiv : 0.f);
+      }
+      if (lbad) bad = 1;
+      // inverse of the block: lane r builds row r of Linv, rows in order
+      float li[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) li[c] = 0.f;
+#pragma unroll
+      for (int k = 0; k < SB; ++k) {
+        const float rd = recip(__shfl_sync(full, a[k], k));
+#pragma unroll
+        for (int c = 0; c <= k; ++c)
+          if (lane == k) li[c] = ((c == k ? 1.f : 0.f) - li[c]) * rd;
+#pragma unroll
+        for (int c = 0; c <= k; ++c) {
+          const float v = __shfl_sync(full, li[c], k);
+          if (lane > k) li[c] += a[k] * v;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        Lib[lane * (SB + 1) + c] = c <= lane ? li[c] : 0.f;
+        if (lane < nb && c < nb && c <= lane) A[(int64_t)(k0 + lane) * lda + k0 + c] = a[c];
+      }
+    }
+    __syncthreads();
+    // panel rows below the block: P[i][c] = sum_{q <= c} A[i][k0+q] Linv[c][q]
+    const int r0 = k0 + SB;
+    for (int i = r0 + warp; i < n; i += STH / 32) {
+      const float av = lane < nb ? A[(int64_t)i * lda + k0 + lane] : 0.f;
+      float pv = 0.f;
+#pragma unroll
+      for (int q = 0; q < SB; ++q) pv += __shfl_sync(full, av, q) * Lib[lane * (SB + 1) + q];
+      P[(size_t)i * SBP + lane] = pv;
+      if (lane < nb) A[(int64_t)i * lda + k0 + lane] = pv;
+    }
+    __syncthreads();
+    // trailing update, lower triangle, 32 x 32 tiles over rows/cols >= r0
+    const int nt = (n - r0 + SB - 1) / SB;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int t = warp; t < ntiles; t += STH / 32) {
+      int I = 0, rem = t;  // tile (I, J), J <= I, row-major over the triangle
+      while (rem > I) {
+        rem -= I + 1;
+        ++I;
+      }
+      const int J = rem;
+      const int j = r0 + J * SB + lane;
+      float pj[SB];
+#pragma unroll
+      for (int q = 0; q < SB; ++q) pj[q] = j < n ? P[(size_t)j * SBP + q] : 0.f;
+      const int ibeg = r0 + I * SB;
+      const int iend = min(n, ibeg + SB);
+      for (int i = ibeg; i < iend; i += 4) {  // four independent rows at a time
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* prow[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) prow[u] = P + (size_t)min(i + u, n - 1) * SBP;
+#pragma unroll
+        for (int q = 0; q < SB; q += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 v = *reinterpret_cast<const float4*>(prow[u] + q);  // broadcast
+            acc[u] = fmaf(v.x, pj[q], acc[u]);
+            acc[u] = fmaf(v.y, pj[q + 1], acc[u]);
+            acc[u] = fmaf(v.z, pj[q + 2], acc[u]);
+            acc[u] = fmaf(v.w, pj[q + 3], acc[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i + u < iend && j < n && j <= i + u) A[(int64_t)(i + u) * lda + j] -= acc[u];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad) set_status(st, VL_ERR_RANK);
+  // 64 x 64 diagonal-block inverses for the blocked solves
+  const int nb64 = (n + CHOL_NB - 1) / CHOL_NB;
+  for (int b = warp; b < nb64; b += STH / 32) {
+    float* out = dinv + (size_t)b * CHOL_NB * CHOL_NB;
+    const int b0 = 2 * b, b1 = 2 * b + 1;
+    const float* Ai = Li + (size_t)b0 * SB * (SB + 1);
+    const bool has1 = b1 < nblk;
+    const float* Ci = has1 ? Li + (size_t)b1 * SB * (SB + 1) : nullptr;
+    // row `lane` of each quadrant
+    for (int c = 0; c < SB; ++c) {
+      out[lane * CHOL_NB + c] = Ai[lane * (SB + 1) + c];                 // A^{-1}
+      out[lane * CHOL_NB + SB + c] = 0.f;                                // 0
+      out[(SB + lane) * CHOL_NB + SB + c] =
+          has1 ? Ci[lane * (SB + 1) + c] : (c == lane ? 1.f : 0.f);      // C^{-1}
+    }
+    // X = -C^{-1} (B A^{-1}), B[r][q] = L[k0 + 32 + r][k0 + q]
+    float tmp[SB];
+    const int k0 = b0 * SB;
+#pragma unroll
+    for (int c = 0; c < SB; ++c) tmp[c] = 0.f;
+    if (has1) {
+      const int r = k0 + SB + lane;  // row of B held by this lane
+      for (int q = 0; q < SB; ++q) {
+        const float bq = r < n ? A[(int64_t)r * lda + k0 + q] : 0.f;
+#pragma unroll
+        for (int c = 0; c < SB; ++c) tmp[c] += bq * Ai[q * (SB + 1) + c];
+      }
+    }
+    // out row (32 + lane): -sum_r Ci[lane][r] tmp_r[c], tmp_r is lane r's tmp
+#pragma unroll
+    for (int c = 0; c < SB; ++c) {
+      float x = 0.f;
+      for (int r = 0; r < SB; ++r) {
+        const float t = __shfl_sync(full, tmp[c], r);
+        x += (has1 ? Ci[lane * (SB + 1) + r] : 0.f) * t;
+      }
+      out[(SB + lane) * CHOL_NB + c] = -x;
+    }
+  }
+}
+
+size_t chol_single_smem(int n) {
+  const int nblk = (n + SB - 1) / SB;
+  return sizeof(float) * ((size_t)n * SBP + (size_t)nblk * SB * (SB + 1));
 }
 
 // ---- Column-parallel blocked triangular solves.  Each CTA owns SC
@@ -537,9 +758,19 @@ void gemm_launch(const Ctx& cx, int M, int N, int K, double alpha, View<T> A, Vi
   if (ks > 1) {
     int64_t tot = (int64_t)M * N;
     note_launch();
-    splitk_reduce_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, cx.s>>>(
-        cx.part, ks, M, N, beta, C, ldc, mode);
+    if constexpr (!SPLIT && sizeof(T) == 4)
+      splitk_reduce_f32_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, cx.s>>>(
+          reinterpret_cast<const float*>(cx.part), ks, M, N, beta, C, ldc, mode);
+    else
+      splitk_reduce_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, cx.s>>>(
+          cx.part, ks, M, N, beta, C, ldc, mode);
   }
+}
+
+// Padded work of an M x N product in BM x BN tiles (relative to M N).
+double tile_waste(int M, int N, int BM, int BN) {
+  const double gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
+  return gm * BM * gn * BN / ((double)M * N);
 }
 
 }  // namespace
@@ -554,10 +785,19 @@ void launch_gemm(const Ctx& cx, int M, int N, int K, double alpha, View<T> A, Vi
                  double beta, TC* C, int64_t ldc, bool lower_only) {
   const int mode = lower_only ? 1 : 0;
   if constexpr (sizeof(T) == 4) {
-    if ((int64_t)M * N >= 256 * 256)
-      gemm_launch<T, TC, 8, 8, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
-    else
+    // largest micro-tile whose padded work stays within 10% of the best
+    if ((int64_t)M * N >= 256 * 256) {
+      const double w8 = tile_waste(M, N, 128, 128), w5 = tile_waste(M, N, 80, 80);
+      const double w4 = tile_waste(M, N, 64, 64);
+      if (w8 <= 1.1 * std::min(w5, w4))
+        gemm_launch<T, TC, 8, 8, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
+      else if (w5 <= 1.1 * w4)
+        gemm_launch<T, TC, 5, 5, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
+      else
+        gemm_launch<T, TC, 4, 4, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
+    } else {
       gemm_launch<T, TC, 4, 4, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode, 512);
+    }
   } else {
     gemm_launch<T, TC, 4, 4, false>(cx, M, N, K, alpha, A, A, B, B, beta, C, ldc, mode,
                                     1 << 30);
@@ -581,6 +821,23 @@ template <class T>
 void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag0) {
   const int NB = CHOL_NB;
   cudaStream_t s = cx.s;
+  if constexpr (sizeof(T) == 4) {
+    if (n <= SINGLE_MAX) {
+      const size_t smem1 = chol_single_smem(SINGLE_MAX);
+      static bool attr1 = false;
+      if (!attr1) {
+        cudaFuncSetAttribute(chol_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem1);
+        attr1 = true;
+      }
+      note_launch();
+      save_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
+      note_launch();
+      chol_single_kernel<<<1, STH, chol_single_smem(n), s>>>(A, lda, n, dinv, diag0, 1e-6f,
+                                                            cx.st);
+      return;
+    }
+  }
   const size_t smem = 2 * CHOL_NB * (CHOL_NB + 1) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
