@@ -401,14 +401,24 @@ constexpr int SBP = SB + 4;  // panel row stride in shared memory (16-byte align
 constexpr int SINGLE_MAX = 512;
 constexpr int STH = 512;
 
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// prof (optional, NULL in the library): three globaltimer stamps per block
+// column (after the diagonal block, the panel and the trailing update).
 __global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A, int64_t lda,
                                                           int n, float* __restrict__ dinv,
                                                           const double* __restrict__ diag0,
-                                                          float rel_tol, int* st) {
+                                                          float rel_tol, int* st,
+                                                          unsigned long long* prof = nullptr) {
   extern __shared__ __align__(16) float cs_smem[];
   const int nblk = (n + SB - 1) / SB;
-  float* P = cs_smem;                             // [n][SBP] panel
-  float* Li = P + (size_t)n * SBP;                // [nblk][SB][SB + 1] block inverses
+  float* P = cs_smem;                      // [max(n, SB)][SBP] panel; rows 0..31 also
+                                           // stage the diagonal tile
+  float* Li = P + (size_t)max(n, SB) * SBP;  // [nblk][SB][SB + 1] block inverses
   __shared__ int bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned full = 0xffffffffu;
@@ -419,11 +429,20 @@ __global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A,
     const int nb = min(SB, n - k0);
     float* Lib = Li + (size_t)b * SB * (SB + 1);
     if (warp == 0) {
+      {  // stage the tile through shared memory: coalesced rows, all in flight
+        float rowv[SB];
+#pragma unroll
+        for (int r = 0; r < SB; ++r)
+          rowv[r] = (r < nb && lane <= r) ? A[(int64_t)(k0 + r) * lda + k0 + lane] : 0.f;
+#pragma unroll
+        for (int r = 0; r < SB; ++r) P[(size_t)r * SBP + lane] = rowv[r];
+      }
+      __syncwarp();
       float a[SB];
 #pragma unroll
       for (int c = 0; c < SB; ++c) {
         float v = (c == lane) ? 1.f : 0.f;  // identity padding
-        if (lane < nb && c < nb && c <= lane) v = A[(int64_t)(k0 + lane) * lda + k0 + c];
+        if (lane < nb && c < nb && c <= lane) v = P[(size_t)lane * SBP + c];
         a[c] = v;
       }
       const float thr = lane < nb ? (float)(rel_tol * diag0[k0 + lane]) : 0.f;
@@ -464,24 +483,43 @@ __global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A,
           if (lane > k) li[c] += a[k] * v;
         }
       }
+      __syncwarp();
 #pragma unroll
       for (int c = 0; c < SB; ++c) {
         Lib[lane * (SB + 1) + c] = c <= lane ? li[c] : 0.f;
-        if (lane < nb && c < nb && c <= lane) A[(int64_t)(k0 + lane) * lda + k0 + c] = a[c];
+        P[(size_t)lane * SBP + c] = a[c];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < SB; ++r)  // write the factor back, coalesced
+        if (r < nb && lane <= r) A[(int64_t)(k0 + r) * lda + k0 + lane] = P[(size_t)r * SBP + lane];
+    }
+    __syncthreads();
+    if (prof && tid == 0) prof[3 * b] = gtimer();
+    // panel rows below the block: P[i][c] = sum_{q <= c} A[i][k0+q] Linv[c][q]
+    const int r0 = k0 + SB;
+    for (int i0 = r0 + 4 * warp; i0 < n; i0 += 4 * (STH / 32)) {  // four rows per warp
+      float av[4], pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = (lane < nb && i0 + u < n) ? A[(int64_t)(i0 + u) * lda + k0 + lane] : 0.f;
+        pv[u] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < SB; ++q) {
+        const float l = Lib[lane * (SB + 1) + q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pv[u] = fmaf(__shfl_sync(full, av[u], q), l, pv[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (i0 + u >= n) continue;
+        P[(size_t)(i0 + u) * SBP + lane] = pv[u];
+        if (lane < nb) A[(int64_t)(i0 + u) * lda + k0 + lane] = pv[u];
       }
     }
     __syncthreads();
-    // panel rows below the block: P[i][c] = sum_{q <= c} A[i][k0+q] Linv[c][q]
-    const int r0 = k0 + SB;
-    for (int i = r0 + warp; i < n; i += STH / 32) {
-      const float av = lane < nb ? A[(int64_t)i * lda + k0 + lane] : 0.f;
-      float pv = 0.f;
-#pragma unroll
-      for (int q = 0; q < SB; ++q) pv += __shfl_sync(full, av, q) * Lib[lane * (SB + 1) + q];
-      P[(size_t)i * SBP + lane] = pv;
-      if (lane < nb) A[(int64_t)i * lda + k0 + lane] = pv;
-    }
-    __syncthreads();
+    if (prof && tid == 0) prof[3 * b + 1] = gtimer();
     // trailing update, lower triangle, 32 x 32 tiles over rows/cols >= r0
     const int nt = (n - r0 + SB - 1) / SB;
     const int ntiles = nt * (nt + 1) / 2;
@@ -499,6 +537,10 @@ __global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A,
       const int ibeg = r0 + I * SB;
       const int iend = min(n, ibeg + SB);
       for (int i = ibeg; i < iend; i += 4) {  // four independent rows at a time
+        float old[4];  // issued before the FMAs so their latency overlaps them
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          old[u] = (i + u < iend && j < n && j <= i + u) ? A[(int64_t)(i + u) * lda + j] : 0.f;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         const float* prow[4];
 #pragma unroll
@@ -516,10 +558,11 @@ __global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A,
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (i + u < iend && j < n && j <= i + u) A[(int64_t)(i + u) * lda + j] -= acc[u];
+          if (i + u < iend && j < n && j <= i + u) A[(int64_t)(i + u) * lda + j] = old[u] - acc[u];
       }
     }
     __syncthreads();
+    if (prof && tid == 0) prof[3 * b + 2] = gtimer();
   }
   if (tid == 0 && bad) set_status(st, VL_ERR_RANK);
   // 64 x 64 diagonal-block inverses for the blocked solves
@@ -565,7 +608,7 @@ __global__ void __launch_bounds__(STH) chol_single_kernel(float* __restrict__ A,
 
 size_t chol_single_smem(int n) {
   const int nblk = (n + SB - 1) / SB;
-  return sizeof(float) * ((size_t)n * SBP + (size_t)nblk * SB * (SB + 1));
+  return sizeof(float) * ((size_t)std::max(n, SB) * SBP + (size_t)nblk * SB * (SB + 1));
 }
 
 // ---- Column-parallel blocked triangular solves.  Each CTA owns SC
