@@ -31,8 +31,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pair-samples/s of pairwise measure; end-to-end ms at m=400 (mixed vs FP64)"
 UNIT = "pair-samples/s"
-ALG_OPS_PER_PAIR_SAMPLE = 18  # see the design doc: 2 x (2 form w, 2 ex2, 1 prod, 1 |w|, 2 exp arg, 1 acc)
-SM_LANES_PER_CLK = 128  # FP32/issue lanes per SM per clock (4 SMSPs x 32)
+# Roofline of the pairwise kernel: the special-function unit (MUFU).  Per
+# pair-sample the method needs, for each of the two residuals, two
+# exponentials (e^{-2|u|} for log cosh, e^{-u^2/2}) and, amortised over a
+# 16-sample run, one logarithm, which issues at half the exponential rate:
+# 2 x (2 + 2/16) = 4.25 exponential-equivalent SFU slots.
+SFU_SLOTS_PER_PAIR_SAMPLE = 4.25
+SFU_PER_SM_CLK = 32  # ex2 results per SM per clock on this part
+# DRAM bytes per launch of the pairwise kernel at m=400, n=2500 from one ncu
+# capture (profiles/pairwise_f32_finance_m400.md), valid only for the kernel
+# source it was taken on: reported as null once the source changes.
+PAIRWISE_TRAFFIC = {"sha1": "2d8028fff11da1afa4d78092fbae136d09ec5bd8",
+                    "bytes": 5389824 + 479488, "m": 400, "n": 2500}
 MAX_SM_MHZ = 2070.0
 
 
@@ -47,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the 256-series mixed-size batch (vl_fit_batched)")
     return ap.parse_args()
 
 
@@ -137,6 +149,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------- multi-rank
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest value of x over all ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job rate: every rank processes units_per_rank per step (weak
+    scaling); the step time is the maximum over ranks."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 # --------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world):
     import numpy as np
@@ -215,13 +245,9 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev)
     ms, kms, launches = timed(args.prec, args.steps, args.warmup, kernel_events=True)
     clk = clocks.stop()
-    tot_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(ms), world, f"cuda:{dev}")
     ms_per_step = tot_ms / args.steps
-    value = world * PS / (ms_per_step * 1e-3)
+    value = job_throughput(PS, world, ms_per_step)
 
     # per-phase split through the four separate calls (one extra step, outside
     # the timed region; vl_fit_b recomputes the covariance there)
@@ -258,28 +284,35 @@ def run_ours(args, rank, world):
         stream.synchronize()
         if k >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_step], dtype=torch.float64, device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, f"cuda:{dev}")
     d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
 
     # roofline of the dominant kernel (pairwise moments), live CUDA events
     k_ms = statistics.mean(kms) if kms else None
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak = sms * SM_LANES_PER_CLK * MAX_SM_MHZ * 1e6 / 1e12  # Tops/s at max clock
+    peak = sms * SFU_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12  # T SFU slots/s at max clock
+    traffic = None
+    try:
+        import hashlib
+
+        src = os.path.join(ROOT, "paper_2409_05500_gb300", "csrc", "k_pairwise.cu")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if (sha == PAIRWISE_TRAFFIC["sha1"] and (m, n) == (PAIRWISE_TRAFFIC["m"], PAIRWISE_TRAFFIC["n"])
+                and args.prec == "mixed"):
+            traffic = PAIRWISE_TRAFFIC["bytes"]
+    except OSError:
+        traffic = None
     roof = None
     if k_ms:
-        ach = PS * ALG_OPS_PER_PAIR_SAMPLE / (k_ms * 1e-3) / 1e12
+        ach = PS * SFU_SLOTS_PER_PAIR_SAMPLE / (k_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
-                "unit": "Tops/s", "frac": round(ach / peak, 4), "traffic": None,
+                "unit": "T SFU-slots/s", "frac": round(ach / peak, 4), "traffic": traffic,
                 "kernel": "pairwise_f32_kernel" if args.prec == "mixed" else "pairwise_f64_kernel",
                 "kernel_ms": round(k_ms, 4),
                 "kernel_pair_samples_per_s": PS / (k_ms * 1e-3),
-                "peak_basis": f"{sms} SMs x {SM_LANES_PER_CLK} lanes/clk x {MAX_SM_MHZ:.0f} MHz; "
-                              f"{ALG_OPS_PER_PAIR_SAMPLE} algorithmic ops per pair-sample"}
+                "peak_basis": f"{sms} SMs x {SFU_PER_SM_CLK} ex2/clk x {MAX_SM_MHZ:.0f} MHz; "
+                              f"{SFU_SLOTS_PER_PAIR_SAMPLE} SFU slots per pair-sample"}
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -292,17 +325,45 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single"},
         "fp64_ms_per_step": fp64_ms,
         "phase_ms": phases,
-        "e2e": {"value": world * PS / (e2e_step * 1e-3), "unit": UNIT, "ms_per_step": e2e_step,
+        "e2e": {"value": job_throughput(PS, world, e2e_step), "unit": UNIT, "ms_per_step": e2e_step,
                 "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
         "clocks": clk,
     }
+    if args.batched:
+        res["batched"] = run_batched(vl, h, torch, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
     h.close()
     return res
+
+
+def run_batched(vl, h, torch, dev, args):
+    """256 independent series of mixed (m, n, p) through one vl_fit_batched
+    call per step; aggregate pair-samples/s over the batch."""
+    import synth
+
+    insts = synth.make_batched(256, synth.config_seed(4))
+    dicts = []
+    for inst in insts:
+        o = vl.alloc_outputs(inst.m, inst.p, dev)
+        o["X"] = torch.from_numpy(inst.X).to(f"cuda:{dev}")
+        o["p"] = inst.p
+        dicts.append(o)
+    ps = sum(pair_samples(i.m, i.n, i.p) for i in insts)
+    for _ in range(2):
+        st = vl.vl_fit_batched(h, dicts, args.prec)
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        st = vl.vl_fit_batched(h, dicts, args.prec)  # synchronises at its end
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    return {"series": len(insts), "pair_samples": ps, "seconds": t, "value": ps / t,
+            "unit": UNIT, "failed": sum(1 for x in st if x != 0),
+            "timing": "host wall clock around the call (it synchronises), best of 3"}
 
 
 def run_reference(args):

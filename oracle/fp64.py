@@ -20,8 +20,8 @@ import scipy.linalg
 # ------------------------------------------------------------------ entropy
 # Maximum-entropy approximation of differential entropy (Hyvarinen 1998) with
 # the two contrast functions G1(u) = log cosh u and G2(u) = u exp(-u^2/2), the
-# form DirectLiNGAM uses.  The paper only says "an entropy approximation"
-# (Section 3, step 3).
+# form DirectLiNGAM uses.  The paper uses an entropy approximation without
+# defining it (Section 3, step 3).
 H_GAUSS = 0.5 * (1.0 + math.log(2.0 * math.pi))  # entropy of N(0, 1)
 ENTROPY_K1 = 79.047  # weight of (E log cosh u - gamma)^2 (literature value)
 ENTROPY_K2 = 7.4129  # weight of (E u exp(-u^2/2))^2 (= 36 / (8 sqrt3 - 9))

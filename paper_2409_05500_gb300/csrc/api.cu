@@ -214,9 +214,9 @@ vl_status pairwise_impl(Exec& x, const double* E, int64_t lde, int m, int n, dou
   const bool f32 = sizeof(T) == 4;
   PairPlan pl = plan_pairwise(m, n, x.h->num_sms, !f32);
   const size_t part_cap = (size_t)16 * m * m;
-  // FP32 path: 6 floats (3 double-float sums) per residual per split;
+  // FP32 path: 4 floats (2 double-float sums) per residual per split;
   // FP64 path: 2 doubles
-  const size_t nparts = (size_t)pl.splits * (f32 ? 3 : 2) * m * m;  // in 8-byte units
+  const size_t nparts = (size_t)pl.splits * 2 * m * m;  // in 8-byte units
   CovOut o;
   void* scratch;
   float *rho32 = nullptr, *c32 = nullptr;

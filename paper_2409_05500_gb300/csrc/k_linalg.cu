@@ -875,6 +875,7 @@ void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag
       }
       note_launch();
       save_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
+      if (launch_chol_cluster(A, lda, n, dinv, diag0, 1e-6f, cx.st, s)) return;
       note_launch();
       chol_single_kernel<<<1, STH, chol_single_smem(n), s>>>(A, lda, n, dinv, diag0, 1e-6f,
                                                             cx.st);

@@ -14,6 +14,7 @@
 // relative gaps are computed after the search by another.  Subtracting the
 // removed column instead of re-summing over U gives the same sums as the
 // literal recomputation up to rounding (~1e-14 relative).
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <mutex>
@@ -26,7 +27,7 @@ namespace vl {
 namespace {
 
 constexpr int OTH = 1024;
-constexpr int PER = (VL_MAX_M + OTH - 1) / OTH;
+static_assert(VL_MAX_M <= 4 * OTH, "ordering holds at most four variables per thread");
 
 // Pt_hi/lo[c * m + i] = min(0, D[i * m + c])^2 as a double-float pair.
 __global__ void pt_kernel(const double* __restrict__ D, int m, float* __restrict__ pth,
@@ -122,20 +123,47 @@ __device__ __forceinline__ Cand warp_min(Cand c) {
 
 __device__ __forceinline__ Cand none() { return Cand{0xffffffffu, 0xffffffffu, INT_MAX}; }
 
-// One CTA, up to 1024 threads, each owning PER variables (i = tid + q*nthr);
-// a step is a two-level argmin (warp REDUX, then warp 0 over the warp
-// winners) and the update S_i -= P_{i,c}.  The P column of the pick is loaded
-// together with the column of the runner-up; when the runner-up wins the next
-// step (about two thirds of the steps on the workloads measured) that step
-// uses the prefetched registers and skips the L2 round trip.
+// Warp-wide lexicographic minimum of (kh, kl, idx), in every lane.  A real
+// score never has the key 0xffffffff (that is a NaN pattern), so a warp whose
+// minimum kh is 0xffffffff holds no live candidate.  Fast path: one lane holds
+// the minimum kh (REDUX + VOTE + SHFL); ties on kh take the full three-key
+// reduction.  *src returns the winning lane (-1 if none).
+__device__ __forceinline__ Cand warp_argmin(const Cand& c, int* src) {
+  const uint32_t full = 0xffffffffu;
+  const uint32_t mh = __reduce_min_sync(full, c.kh);
+  if (mh == 0xffffffffu) {
+    *src = -1;
+    return none();
+  }
+  const uint32_t bal = __ballot_sync(full, c.kh == mh);
+  if (__popc(bal) == 1) {
+    const int l = __ffs(bal) - 1;
+    *src = l;
+    return Cand{mh, __shfl_sync(full, c.kl, l), __shfl_sync(full, c.idx, l)};
+  }
+  const Cand w = warp_min(c);
+  *src = __ffs(__ballot_sync(full, c.idx == w.idx && c.kh == w.kh && c.kl == w.kl)) - 1;
+  return w;
+}
+
+// One CTA of up to 1024 threads, each owning PER variables (i = tid + q*nthr).
+// A step: every warp finds its best and runner-up (warp_argmin), writes them
+// to a shared slot of the step's parity, one barrier, then every warp reduces
+// the warp winners itself, so all threads learn the pick c and the runner-up
+// r without a second barrier (slots alternate by parity: a warp can run at
+// most one step ahead of the slowest).  Then S_i -= P_{i,c}.  The P column of
+// the pick is loaded together with the column of the runner-up; when the
+// runner-up wins the next step (about 60% of the steps on the workloads
+// measured) that step uses the prefetched registers and skips the L2 round
+// trip.
+template <int PER>
 __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pth,
                                                     const float* __restrict__ ptl,
                                                     const float* __restrict__ sh0,
                                                     const float* __restrict__ sl0, int m,
                                                     int32_t* __restrict__ order,
                                                     float4* __restrict__ best2) {
-  __shared__ Cand wb1[32], wb2[32];
-  __shared__ int s_c, s_r;
+  __shared__ Cand wb1[2][32], wb2[2][32];
   const int nthr = blockDim.x, nw = (nthr + 31) >> 5;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float hi[PER], lo[PER], nh[PER], nl[PER];
@@ -150,41 +178,46 @@ __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pt
   }
   int pre = -1;
   for (int k = 0; k < m; ++k) {
+    const int ph = k & 1;
+    // this thread's best and runner-up
     Cand b1 = none(), b2 = none();
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       if (!alive[q]) continue;
-      Cand c{fkey(hi[q]), fkey(lo[q]), (int)threadIdx.x + q * nthr};
-      if (cless(c, b1)) {
+      const Cand c{fkey(hi[q]), fkey(lo[q]), (int)threadIdx.x + q * nthr};
+      if (PER == 1) {
+        b1 = c;
+      } else if (cless(c, b1)) {
         b2 = b1;
         b1 = c;
       } else if (cless(c, b2)) {
         b2 = c;
       }
     }
-    Cand w1 = warp_min(b1);
-    Cand w2 = warp_min((b1.idx == w1.idx) ? b2 : b1);
-    if (lane == 0) {
-      wb1[wid] = w1;
-      wb2[wid] = w2;
-    }
+    // warp level: the winning lane writes its own candidate
+    int l1, l2;
+    warp_argmin(b1, &l1);
+    const Cand s2 = (lane == l1) ? b2 : b1;
+    warp_argmin(s2, &l2);
+    if (lane == 0 && l1 < 0) wb1[ph][wid] = none();
+    if (lane == l1) wb1[ph][wid] = b1;
+    if (lane == 0 && l2 < 0) wb2[ph][wid] = none();
+    if (lane == l2) wb2[ph][wid] = s2;
     __syncthreads();
-    if (wid == 0) {
-      Cand a1 = lane < nw ? wb1[lane] : none();
-      Cand a2 = lane < nw ? wb2[lane] : none();
-      Cand g1 = warp_min(a1);
-      Cand g2 = warp_min((a1.idx == g1.idx) ? a2 : a1);
-      if (lane == 0) {
-        s_c = g1.idx;
-        s_r = g2.idx;
-        order[k] = g1.idx;
-        best2[k] = make_float4(fkey_inv(g1.kh), fkey_inv(g1.kl),
-                               g2.idx == INT_MAX ? __int_as_float(0x7f800000) : fkey_inv(g2.kh),
-                               g2.idx == INT_MAX ? 0.f : fkey_inv(g2.kl));
-      }
+    // block level, redundantly in every warp
+    const Cand a1 = lane < nw ? wb1[ph][lane] : none();
+    const Cand a2 = lane < nw ? wb2[ph][lane] : none();
+    int g1l, g2l;
+    const Cand g1 = warp_argmin(a1, &g1l);
+    const int c = g1.idx;
+    const Cand g2 = warp_argmin((lane == g1l) ? a2 : a1, &g2l);
+    const int r = g2.idx;
+    if (threadIdx.x == 0) {
+      order[k] = c;
+      best2[k] = make_float4(fkey_inv(g1.kh), fkey_inv(g1.kl),
+                             r == INT_MAX ? __int_as_float(0x7f800000) : fkey_inv(g2.kh),
+                             r == INT_MAX ? 0.f : fkey_inv(g2.kl));
     }
-    __syncthreads();
-    const int c = s_c, r = s_r;
     float ch[PER], cl[PER];
     if (c == pre) {
 #pragma unroll
@@ -255,10 +288,16 @@ void launch_causal_order(const double* D, int m, void* ws, int32_t* order, doubl
   pt_kernel<<<grid, block, 0, s>>>(D, m, pth, ptl, st);
   note_launch();
   rowsum_kernel<<<(m + 7) / 8, 256, 0, s>>>(D, m, sh, sl);
-  int nthr = (m + 31) / 32 * 32;  // one variable per thread up to 1024
-  if (nthr > OTH) nthr = OTH;
+  // variables per thread: PER = 1 up to 1024 variables, then 2 and 4
+  const int per = m <= OTH ? 1 : (m <= 2 * OTH ? 2 : 4);
+  const int nthr = std::min(OTH, ((m + per - 1) / per + 31) / 32 * 32);
   note_launch();
-  order_kernel<<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+  if (per == 1)
+    order_kernel<1><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+  else if (per == 2)
+    order_kernel<2><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+  else
+    order_kernel<4><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
   if (gap) {
     note_launch();
     gap_kernel<<<(m + 255) / 256, 256, 0, s>>>(best2, m, gap);

@@ -11,17 +11,21 @@
 //     w    = kappa s r                  kappa = 2 log2(e), so 2^{-|w|} = e^{-2|u|}
 //     y    = ex2(-|w|)                  (MUFU)
 //     prod = prod * (1 + y)             log cosh u = |u| + ln(1 + y) - ln 2
-//     sa  += |w|
+//     ra  += |w|
 //     g    = ex2(-w^2 / (8 log2 e))     = e^{-u^2/2}   (MUFU)
-//     sb  += w g
-// Every KRUN = 16 samples the run sums are Kahan-added into FP32 (sum, comp)
-// pairs and log2(prod) (one MUFU lg2 per run) is Kahan-added as well, so
-// sum_t ln(1 + y_t) = ln 2 * sum_runs log2(prod_run).  The split partials are
-// written as FP64 and combined in a fixed order by measure_finalize.
+//     rb  += w g
+// Every KRUN = 16 samples the run's log-cosh sum
+//     sum_t log cosh u_t = ra / kappa + ln 2 (log2(prod) - 16)
+// (one MUFU lg2 per run) and its sb are Kahan-added into FP32 (sum, comp)
+// pairs.  The two j's of a thread's micro-tile are processed as one float2
+// with the paired FP32 instructions of this architecture (fma/mul/add .f32x2),
+// which halves the FP32 instruction count; the exponentials stay scalar MUFU.
+// The split partials are combined in double-float arithmetic by
+// measure_finalize.
 //
 // Padding: x is zero beyond n (time) and beyond m (variables).  A zero sample
-// gives |w| = 0, 1 + y = 2, w g = 0, i.e. exactly log cosh 0 = 0 once the
-// ln 2 per processed sample is removed, so padding needs no masking.
+// gives |w| = 0, 1 + y = 2 (log2 adds exactly 1, cancelled by the -16 per
+// run) and w g = 0, i.e. it contributes exactly 0: padding needs no masking.
 #include <algorithm>
 #include <cmath>
 
@@ -34,7 +38,7 @@ namespace {
 constexpr int TB = 32;        // variables per tile side
 constexpr int TT = 128;       // samples per shared-memory stage
 constexpr int KRUN = 16;      // samples per product/Kahan run (product <= 2^16)
-constexpr int NTH = 256;      // threads: 16 x 16, each a 2 x 2 pair micro-tile
+constexpr int NTH = 256;      // FP64 kernel threads: 16 x 16, each a 2 x 2 pair micro-tile
 constexpr float KAPPA = 2.8853900817779268f;       // 2 log2(e)
 constexpr float GAUSS_K = -0.08664339756999316f;   // -1 / (8 log2 e)
 
@@ -47,12 +51,6 @@ __device__ __forceinline__ float lg2_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-__device__ __forceinline__ void kahan_add(float& S, float& C, float x) {
-  float y = x - C;
-  float t = S + y;
-  C = (t - S) - y;
-  S = t;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -76,26 +74,43 @@ __device__ __forceinline__ void tile_coords(int q, int T, int& I, int& J) {
   J = i + rem;
 }
 
-struct Stream {
-  float sa, ca, sb, cb, sl, cl;
+// State of two residual streams (the two j's of a micro-tile row), as float2.
+struct Pair2 {
+  float2 prod, ra, rb;      // current 16-sample run
+  float2 sa, ca, sb, cb;    // Kahan (sum, compensation) of the run sums
 };
 
-// Thread -> 2 x 2 pair micro-tile (ti, tj) of tile (I, J), enumerating only
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// (S, C) += x, Kahan, both lanes at once
+__device__ __forceinline__ void kahan2(float2& S, float2& C, float2 x) {
+  const float2 mone = f2(-1.f, -1.f);
+  const float2 y = __ffma2_rn(C, mone, x);  // x - C
+  const float2 t = __fadd2_rn(S, y);
+  C = __ffma2_rn(y, mone, __ffma2_rn(S, mone, t));  // (t - S) - y
+  S = t;
+}
+
+// Thread -> MTI x 2 pair micro-tile (ti, tj) of tile (I, J), enumerating only
 // micro-tiles holding at least one pair i < j < m; returns false for threads
-// beyond that count.
+// beyond that count.  Micro-tile (ti, tj) covers i = MTI ti + a, j = 2 tj + b.
+template <int MTI>
 __device__ __forceinline__ bool micro_tile(int s, int I, int J, int m, int& ti, int& tj) {
+  constexpr int R = TB / MTI;                     // micro-rows
   const int lim = min(16, (m - J * TB + 1) / 2);  // micro-columns with some j < m
   if (I < J) {
     ti = s / lim;
     tj = s % lim;
-    if (ti < 16) return true;
+    if (ti < R) return true;
   } else {
-    // upper triangle ti <= tj < lim, row by row
-    for (int r = 0; r < lim; ++r) {
-      const int len = lim - r;
+    // diagonal tile: row ti needs 2 tj + 1 > MTI ti, i.e. tj >= (MTI ti + 1) / 2
+    for (int r = 0; r < R; ++r) {
+      const int st = (MTI * r + 1) / 2;
+      const int len = lim - st;
+      if (len <= 0) break;
       if (s < len) {
         ti = r;
-        tj = r + s;
+        tj = st + s;
         return true;
       }
       s -= len;
@@ -106,42 +121,84 @@ __device__ __forceinline__ bool micro_tile(int s, int I, int J, int m, int& ti, 
   return false;
 }
 
-__global__ void __launch_bounds__(NTH, 2)
+// One sample of one stream pair: residual R (both lanes), scale C.
+__device__ __forceinline__ void step2(Pair2& q, float2 R, float2 C, float2 KK) {
+  const float2 W = __fmul2_rn(C, R);
+  const float2 Y = f2(ex2_approx(-fabsf(W.x)), ex2_approx(-fabsf(W.y)));
+  q.prod = __ffma2_rn(q.prod, Y, q.prod);
+  q.ra.x += fabsf(W.x);
+  q.ra.y += fabsf(W.y);
+  const float2 E = __fmul2_rn(__fmul2_rn(W, KK), W);
+  const float2 G = f2(ex2_approx(E.x), ex2_approx(E.y));
+  q.rb = __ffma2_rn(W, G, q.rb);
+}
+
+__device__ __forceinline__ void end_run2(Pair2& q) {
+  const float2 L = f2(lg2_approx(q.prod.x), lg2_approx(q.prod.y));
+  const float ik = 1.f / KAPPA;
+  const float m16 = -16.f * 0.69314718055994531f;
+  // sum log cosh over the run = ra / kappa + ln 2 (log2 prod - 16)
+  const float2 run =
+      __ffma2_rn(L, f2(0.69314718055994531f, 0.69314718055994531f),
+                 __ffma2_rn(q.ra, f2(ik, ik), f2(m16, m16)));
+  kahan2(q.sa, q.ca, run);
+  kahan2(q.sb, q.cb, q.rb);
+  q.prod = f2(1.f, 1.f);
+  q.ra = f2(0.f, 0.f);
+  q.rb = f2(0.f, 0.f);
+}
+
+// MTI x 2 pair micro-tiles, (32 / MTI) x 16 threads per 32 x 32 tile, TTS
+// samples per shared-memory stage, MINB CTAs per SM.
+template <int MTI, int TTS, int MINB>
+__global__ void __launch_bounds__(TB / MTI * 16, MINB)
     pairwise_f32_kernel(const float* __restrict__ xt, int m, int m_pad, int T, int n_run,
                         int tps, const float* __restrict__ rho32,
                         const float* __restrict__ c32, float* __restrict__ part) {
+  constexpr int NT = TB / MTI * 16;
   extern __shared__ __align__(16) float pw_smem[];
-  float(*sx)[TT][2 * TB] = reinterpret_cast<float(*)[TT][2 * TB]>(pw_smem);  // [2][TT][64]
+  float(*sx)[TTS][2 * TB] = reinterpret_cast<float(*)[TTS][2 * TB]>(pw_smem);  // [2][TTS][64]
   int I, J;
   tile_coords(blockIdx.x, T, I, J);
   const int split = blockIdx.y;
   const int t0 = split * tps;
   const int t1 = min(n_run, t0 + tps);
 
-  // Valid 2 x 2 pair micro-tiles first: on a diagonal tile only ti <= tj,
+  // Valid micro-tiles first: on a diagonal tile only those with some i < j,
   // on the last tile column only j < m; threads past the valid count (whole
   // warps, at the end) skip the arithmetic and only help stage the samples.
   int ti, tj;
-  const bool active = micro_tile(threadIdx.x, I, J, m, ti, tj);
-  const int li = 2 * ti, lj = 2 * tj;
+  const bool active = micro_tile<MTI>(threadIdx.x, I, J, m, ti, tj);
+  const int li = MTI * ti, lj = 2 * tj;
   const int gi0 = I * TB + li, gj0 = J * TB + lj;
 
-  float rho[4], cc[4];
-  bool valid[4];
+  // pair (a, b) = (i0 + a, j0 + b); constants as float2 over b
+  float2 NR[MTI], C[MTI];
+  bool valid[MTI][2];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int a = gi0 + (p >> 1), b = gj0 + (p & 1);
-    valid[p] = active && (a < b) && (b < m);
-    rho[p] = valid[p] ? rho32[(int64_t)a * m + b] : 0.f;
-    cc[p] = valid[p] ? c32[(int64_t)a * m + b] : KAPPA;
+  for (int a = 0; a < MTI; ++a) {
+    float r2[2], c2[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int gi = gi0 + a, gj = gj0 + b;
+      valid[a][b] = active && (gi < gj) && (gj < m);
+      r2[b] = valid[a][b] ? rho32[(int64_t)gi * m + gj] : 0.f;
+      c2[b] = valid[a][b] ? c32[(int64_t)gi * m + gj] : KAPPA;
+    }
+    NR[a] = f2(-r2[0], -r2[1]);
+    C[a] = f2(c2[0], c2[1]);
   }
-  Stream st[8];
+  const float2 KK = f2(GAUSS_K, GAUSS_K);
+  // stream pairs: 2a = residuals of i_a on (j0, j1), 2a + 1 = of (j0, j1) on i_a
+  Pair2 q[2 * MTI];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) st[q] = Stream{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < 2 * MTI; ++k)
+    q[k] = Pair2{f2(1.f, 1.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f),
+                 f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
 
-  // stage loader: TT rows x (32 + 32) floats = TT * 16 chunks of 16 B
+  // stage loader: TTS rows x (32 + 32) floats = TTS * 16 chunks of 16 B
   auto load_stage = [&](int buf, int tb) {
-    for (int idx = threadIdx.x; idx < TT * 16; idx += NTH) {
+    for (int idx = threadIdx.x; idx < TTS * 16; idx += NT) {
       const int r = idx >> 4, c = idx & 15;  // c: 0-7 I block, 8-15 J block
       const int t = tb + r;
       if (t < t1) {
@@ -154,76 +211,61 @@ __global__ void __launch_bounds__(NTH, 2)
 
   int buf = 0;
   if (t0 < t1) load_stage(0, t0);
-  for (int tb = t0; tb < t1; tb += TT) {
-    const int rows = min(TT, t1 - tb);
-    if (tb + TT < t1) {
-      load_stage(buf ^ 1, tb + TT);
+  for (int tb = t0; tb < t1; tb += TTS) {
+    const int rows = min(TTS, t1 - tb);
+    if (tb + TTS < t1) {
+      load_stage(buf ^ 1, tb + TTS);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
     for (int r0 = 0; active && r0 < rows; r0 += KRUN) {
-      float ra[8], rb[8], pr[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        ra[q] = 0.f;
-        rb[q] = 0.f;
-        pr[q] = 1.f;
-      }
 #pragma unroll
       for (int k = 0; k < KRUN; ++k) {
-        const float2 xi = *reinterpret_cast<const float2*>(&sx[buf][r0 + k][li]);
         const float2 xj = *reinterpret_cast<const float2*>(&sx[buf][r0 + k][TB + lj]);
-        const float xa[2] = {xi.x, xi.y}, xb[2] = {xj.x, xj.y};
+        float xi[MTI];
+        if constexpr (MTI == 2) {
+          const float2 v = *reinterpret_cast<const float2*>(&sx[buf][r0 + k][li]);
+          xi[0] = v.x;
+          xi[1] = v.y;
+        } else {
+          xi[0] = sx[buf][r0 + k][li];
+        }
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float a = xa[p >> 1], b = xb[p & 1];
-#pragma unroll
-          for (int d = 0; d < 2; ++d) {
-            const int q = 2 * p + d;
-            const float self = d ? b : a, other = d ? a : b;
-            const float r = fmaf(-rho[p], other, self);
-            const float w = cc[p] * r;
-            const float y = ex2_approx(-fabsf(w));
-            pr[q] = fmaf(pr[q], y, pr[q]);
-            ra[q] += fabsf(w);
-            const float g = ex2_approx((w * GAUSS_K) * w);
-            rb[q] = fmaf(w, g, rb[q]);
-          }
+        for (int a = 0; a < MTI; ++a) {
+          const float2 xa = f2(xi[a], xi[a]);
+          step2(q[2 * a], __ffma2_rn(NR[a], xj, xa), C[a], KK);      // x_i - rho x_j
+          step2(q[2 * a + 1], __ffma2_rn(NR[a], xa, xj), C[a], KK);  // x_j - rho x_i
         }
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        kahan_add(st[q].sa, st[q].ca, ra[q]);
-        kahan_add(st[q].sb, st[q].cb, rb[q]);
-        kahan_add(st[q].sl, st[q].cl, lg2_approx(pr[q]));
-      }
+      for (int k = 0; k < 2 * MTI; ++k) end_run2(q[k]);
     }
     __syncthreads();
     buf ^= 1;
   }
 
-  // partial sums of this split as exact double-float pairs (sum, -comp):
-  // part[(split*6 + k) * m*m + a*m + b] for the residual of a on b.  No FP64
-  // arithmetic here: FP64 issues at 1/64 rate on this part, and a CTA covers
-  // only a few hundred samples.
+  // partials of this split as exact double-float pairs (sum, -comp):
+  // part[(split*4 + k) * m*m + a*m + b] for the residual of a on b, k = 0, 1:
+  // sum of log cosh u; k = 2, 3: sum of w e^{-u^2/2}.  No FP64 arithmetic here.
   const int64_t mm = (int64_t)m * m;
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    if (!valid[p]) continue;
-    const int a = gi0 + (p >> 1), b = gj0 + (p & 1);
+  for (int a = 0; a < MTI; ++a) {
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      const Stream& s = st[2 * p + d];
-      const int64_t off = d ? ((int64_t)b * m + a) : ((int64_t)a * m + b);
-      float* base = part + (int64_t)split * 6 * mm + off;
-      base[0] = s.sa;
-      base[mm] = -s.ca;
-      base[2 * mm] = s.sl;
-      base[3 * mm] = -s.cl;
-      base[4 * mm] = s.sb;
-      base[5 * mm] = -s.cb;
+    for (int b = 0; b < 2; ++b) {
+      if (!valid[a][b]) continue;
+      const int gi = gi0 + a, gj = gj0 + b;
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const Pair2& st = q[2 * a + d];
+        const int64_t off = d ? ((int64_t)gj * m + gi) : ((int64_t)gi * m + gj);
+        float* base = part + (int64_t)split * 4 * mm + off;
+        base[0] = b ? st.sa.y : st.sa.x;
+        base[mm] = -(b ? st.ca.y : st.ca.x);
+        base[2 * mm] = b ? st.sb.y : st.sb.x;
+        base[3 * mm] = -(b ? st.cb.y : st.cb.x);
+      }
     }
   }
 }
@@ -318,7 +360,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 }
 
 __global__ void measure_finalize_kernel(const void* __restrict__ part_v, int m, int splits,
-                                        int n_real, int n_proc, const double* __restrict__ hx,
+                                        int n_real, const double* __restrict__ hx,
                                         double* __restrict__ Hx, double* __restrict__ Hr,
                                         double* __restrict__ D, int fp32_parts) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -339,22 +381,19 @@ __global__ void measure_finalize_kernel(const void* __restrict__ part_v, int m, 
     if (fp32_parts) {
       // splits combined in double-float FP32 arithmetic, one FP64 conversion
       const float* part = static_cast<const float*>(part_v);
-      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
       for (int s = 0; s < splits; ++s) {
-        const float* p = part + (int64_t)s * 6 * mm + off;
+        const float* p = part + (int64_t)s * 4 * mm + off;
         df_add(h0, l0, p[0]);
         df_add(h0, l0, p[mm]);
         df_add(h1, l1, p[2 * mm]);
         df_add(h1, l1, p[3 * mm]);
-        df_add(h2, l2, p[4 * mm]);
-        df_add(h2, l2, p[5 * mm]);
       }
-      const double s0 = (double)h0 + (double)l0;
-      const double s1 = (double)h1 + (double)l1;
-      const double s2 = (double)h2 + (double)l2;
+      const double s0 = (double)h0 + (double)l0;  // sum of log cosh u
+      const double s1 = (double)h1 + (double)l1;  // sum of w e^{-u^2/2}
       const double kappa = 2.0 * LOG2E;
-      A = (s0 / kappa + LN2 * (s1 - (double)n_proc)) / n_real;
-      B = s2 / (kappa * n_real);
+      A = s0 / n_real;
+      B = s1 / (kappa * n_real);
     } else {
       const double* part = static_cast<const double*>(part_v);
       double s0 = 0.0, s1 = 0.0;
@@ -376,7 +415,17 @@ __global__ void measure_finalize_kernel(const void* __restrict__ part_v, int m, 
 
 }  // namespace
 
-PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64) {
+// FP32 kernel configuration: micro-tile rows, samples per stage, CTAs per SM.
+// 1 x 2 micro-tiles, 512 threads and one CTA per SM: measured at m = 400,
+// n = 2500 against 2 x 2 micro-tiles with 256 threads (one or two CTAs per SM)
+// and 64-192 sample stages, this was the fastest (148 vs 150-164 us).
+constexpr int F32_MTI = 1;
+constexpr int F32_TTS = 128;
+constexpr int F32_MINB = 1;
+
+// Sample splits for `slots` resident CTAs: the CTA count should fill whole
+// waves (about 3-6 of them), each split at least two stages of `tts` long.
+PairPlan plan_pairwise_slots(int m, int n, int slots, int tts, bool fp64, int num_sms) {
   PairPlan pl{};
   pl.m = m;
   pl.n = n;
@@ -384,10 +433,7 @@ PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64) {
   const int Tside = pl.m_pad / TB;
   pl.tiles = Tside * (Tside + 1) / 2;
   const int n_run = ((n + KRUN - 1) / KRUN) * KRUN;
-  // Split the samples so that the CTA count fills whole waves of 2 CTAs per
-  // SM (about 3-6 waves), each split at least 2 stages long.
-  const int slots = 2 * num_sms;
-  const int max_split = std::max(1, n_run / (2 * TT));
+  const int max_split = std::max(1, n_run / (2 * tts));
   int splits = 1;
   double best = -1.0;
   for (int sp = 1; sp <= max_split; ++sp) {
@@ -407,8 +453,12 @@ PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64) {
   tps = ((tps + KRUN - 1) / KRUN) * KRUN;
   pl.splits = (n_run + tps - 1) / tps;
   pl.t_per_split = tps;
-  pl.n_pad = ((n_run + TT - 1) / TT) * TT;
+  pl.n_pad = ((n_run + 255) / 256) * 256;  // whole stages of any configuration
   return pl;
+}
+
+PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64) {
+  return plan_pairwise_slots(m, n, F32_MINB * num_sms, F32_TTS, fp64, num_sms);
 }
 
 void launch_pair_consts(const double* C, int m, float* rho32, float* c32, double* rho64, int* st,
@@ -418,20 +468,26 @@ void launch_pair_consts(const double* C, int m, float* rho32, float* c32, double
   pair_consts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, rho32, c32, rho64, st);
 }
 
-void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32,
-                         const float* c32, float* part, cudaStream_t s) {
+template <int MTI, int TTS, int MINB>
+void launch_pairwise_f32_cfg(const float* xt, const PairPlan& pl, const float* rho32,
+                             const float* c32, float* part, cudaStream_t s) {
   const int n_run = ((pl.n + KRUN - 1) / KRUN) * KRUN;
   dim3 grid(pl.tiles, pl.splits);
-  const size_t smem = sizeof(float) * 2 * TT * 2 * TB;  // two stages of TT x 64 samples
+  const size_t smem = sizeof(float) * 2 * TTS * 2 * TB;  // two stages of TTS x 64 samples
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(pairwise_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(pairwise_f32_kernel<MTI, TTS, MINB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
   note_launch();
-  pairwise_f32_kernel<<<grid, NTH, smem, s>>>(xt, pl.m, pl.m_pad, pl.m_pad / TB, n_run,
-                                              pl.t_per_split, rho32, c32, part);
+  pairwise_f32_kernel<MTI, TTS, MINB><<<grid, TB / MTI * 16, smem, s>>>(
+      xt, pl.m, pl.m_pad, pl.m_pad / TB, n_run, pl.t_per_split, rho32, c32, part);
+}
+
+void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32,
+                         const float* c32, float* part, cudaStream_t s) {
+  launch_pairwise_f32_cfg<F32_MTI, F32_TTS, F32_MINB>(xt, pl, rho32, c32, part, s);
 }
 
 void launch_pairwise_f64(const double* xt, const PairPlan& pl, const double* rho64,
@@ -446,10 +502,9 @@ void launch_measure_finalize(const void* part, const PairPlan& pl, const double*
                              double* Hx, double* Hr, double* D, bool fp32_parts,
                              cudaStream_t s) {
   const int64_t tot = (int64_t)pl.m * pl.m;
-  const int n_run = ((pl.n + KRUN - 1) / KRUN) * KRUN;
   note_launch();
   measure_finalize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      part, pl.m, pl.splits, pl.n, n_run, hx_mom, Hx, Hr, D, fp32_parts ? 1 : 0);
+      part, pl.m, pl.splits, pl.n, hx_mom, Hx, Hr, D, fp32_parts ? 1 : 0);
 }
 
 }  // namespace vl

@@ -153,6 +153,11 @@ size_t gemm_part_need(int M, int N, int K);
 // dinv (T, ceil(n/nb) blocks of nb*nb).  diag0 (n doubles) receives the
 // original diagonal; a pivot below 1e-6 (FP32) / 1e-12 (FP64) of it sets
 // VL_ERR_RANK.
+// Cholesky of an FP32 matrix with n <= 512 on one thread-block cluster; false
+// if not launched (n out of range or no cluster resources).
+bool launch_chol_cluster(float* A, int64_t lda, int n, float* dinv, const double* diag0,
+                         float rel_tol, int* st, cudaStream_t s,
+                         unsigned long long* prof = nullptr);
 template <class T>
 void chol_blocked(const Ctx& c, T* A, int64_t lda, int n, T* dinv, double* diag0);
 // Solve L Y = R (forward) then optionally L^T X = Y (backward) for nrhs

@@ -82,12 +82,13 @@ def draw_dag(rng: np.random.Generator, m: int, edge_prob: float, lo: float, hi: 
     """Random DAG under a random causal order perm: edge perm[a] -> perm[b]
     (a < b) with probability edge_prob, weight +-U[lo, hi]."""
     perm = rng.permutation(m)
+    edge = rng.random((m, m)) < edge_prob
+    mag = rng.uniform(lo, hi, size=(m, m))
+    sgn = np.where(rng.random((m, m)) < 0.5, -1.0, 1.0)
+    a_idx, b_idx = np.triu_indices(m, 1)  # a < b in the causal order
+    keep = edge[a_idx, b_idx]
     B0 = np.zeros((m, m))
-    for b in range(m):
-        for a in range(b):
-            if rng.random() < edge_prob:
-                w = rng.uniform(lo, hi) * (1.0 if rng.random() < 0.5 else -1.0)
-                B0[perm[b], perm[a]] = w
+    B0[perm[b_idx[keep]], perm[a_idx[keep]]] = (mag * sgn)[a_idx, b_idx][keep]
     return B0, perm
 
 

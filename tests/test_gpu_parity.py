@@ -277,3 +277,46 @@ def test_bad_arguments(vl, h):
     lib = vl.lib()
     assert lib.vl_causal_order(h.h, None, 4, None, None) == 1
     assert lib.vl_pairwise_measure(h.h, None, 10, 4, 10, 1, None, None, None) == 1
+
+
+# ------------------------------------------------------- batched workload
+def test_batched_workload_parity(vl, h):
+    """The mixed-size batch (the first 48 series of the seeded 256-series
+    draw: m in 20..400, n in 250..5000, p in 1..3, uniform/Laplace/t3 shocks)
+    in one vl_fit_batched call.  Every series: valid order, antisymmetric D,
+    B0 strictly lower triangular in its order, finite B_tau.  A sample (the
+    four smallest and the largest series) against the full FP64 oracle."""
+    insts = synth.make_batched(48, synth.config_seed(4))
+    dicts = []
+    for inst in insts:
+        o = vl.alloc_outputs(inst.m, inst.p)
+        o["X"] = torch.from_numpy(inst.X).cuda()
+        o["p"] = inst.p
+        dicts.append(o)
+    status = vl.vl_fit_batched(h, dicts, "mixed")
+    assert all(s == 0 for s in status), status
+    for inst, o in zip(insts, dicts):
+        order = o["order"].cpu().numpy()
+        assert sorted(order.tolist()) == list(range(inst.m))
+        D = o["D"].cpu().numpy()
+        assert np.allclose(D, -D.T, atol=1e-12 * np.abs(D).max()) and np.all(np.diag(D) == 0)
+        B0 = o["B0"].cpu().numpy()
+        assert np.all(np.triu(B0[np.ix_(order, order)]) == 0)
+        assert np.all(np.isfinite(o["Btau"].cpu().numpy()))
+    by_size = sorted(range(len(insts)), key=lambda k: insts[k].m * insts[k].m * insts[k].n)
+    for k in by_size[:4] + by_size[-1:]:
+        inst, o = insts[k], dicts[k]
+        M, E = oracle.var_ols(inst.X, inst.p)
+        ref = oracle.pairwise_measure(oracle.standardize(E))
+        D = o["D"].cpu().numpy()
+        dmax = np.abs(ref["D"]).max()
+        assert np.abs(D - ref["D"]).max() <= D_REL * dmax
+        order = o["order"].cpu().numpy()
+        ok, ties, bad = oracle.order_gap_ok(order, ref["D"], GAP)
+        assert ok, (k, bad)
+        B0_ref = oracle.b0_ols(E, order)
+        assert np.abs(o["B0"].cpu().numpy() - B0_ref).max() <= B_ABS
+        assert np.abs(o["Btau"].cpu().numpy() - oracle.btau(B0_ref, M)).max() <= B_ABS
+        _report(f"batched #{k} m={inst.m} n={inst.n} p={inst.p}",
+                d_rel=np.abs(D - ref["D"]).max() / dmax, near_ties=ties,
+                b0_err=np.abs(o["B0"].cpu().numpy() - B0_ref).max())
