@@ -8,8 +8,10 @@
 // on this part, so the running sums S_i = M_i are kept as double-float pairs
 // (hi + lo, two FP32 numbers, ~48-bit significand) and updated with TwoSum
 // after each pick, S_i -= P_{i,c}.  The argmin compares an order-preserving
-// 64-bit integer key built from (hi, lo) with the warp reduction instruction
-// (__reduce_min_sync), so no floating-point compare sits on the critical path.
+// 64-bit integer key built from (hi, lo) and the index with two warp
+// reduction instructions (__reduce_min_sync) and no branch, so no
+// floating-point compare sits on the critical path; scores closer than about
+// 2^-35 relative are taken as tied and go by index.
 // The initial sums are computed in FP64 by a parallel kernel; the per-step
 // relative gaps are computed after the search by another.  Subtracting the
 // removed column instead of re-summing over U gives the same sums as the
@@ -28,6 +30,7 @@ namespace {
 
 constexpr int OTH = 1024;
 static_assert(VL_MAX_M <= 4 * OTH, "ordering holds at most four variables per thread");
+static_assert(VL_MAX_M <= 4096, "the search key holds the variable index in 12 bits");
 
 // Pt_hi/lo[c * m + i] = min(0, D[i * m + c])^2 as a double-float pair.
 __global__ void pt_kernel(const double* __restrict__ D, int m, float* __restrict__ pth,
@@ -82,10 +85,6 @@ __device__ __forceinline__ uint32_t fkey(float f) {
   uint32_t b = __float_as_uint(f);
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-__device__ __forceinline__ float fkey_inv(uint32_t k) {
-  uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-  return __uint_as_float(b);
-}
 
 // (hi, lo) -= (ph, pl) in double-float, renormalised so |lo| <= ulp(hi)/2
 // (then the pair order equals the order of (key(hi), key(lo))).
@@ -99,148 +98,75 @@ __device__ __forceinline__ void df_sub(float& hi, float& lo, float ph, float pl)
   hi = h2;
 }
 
-struct Cand {
-  uint32_t kh, kl;  // key of (hi, lo)
-  int idx;
-};
-
-__device__ __forceinline__ bool cless(const Cand& a, const Cand& b) {
-  if (a.kh != b.kh) return a.kh < b.kh;
-  if (a.kl != b.kl) return a.kl < b.kl;
-  return a.idx < b.idx;
+// clock64 read ordered after `dep` is available
+__device__ __forceinline__ long long clock_after(float dep) {
+  long long t;
+  asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : "f"(dep));
+  return t;
 }
 
-// lexicographic warp-wide minimum of (kh, kl, idx) with REDUX
-__device__ __forceinline__ Cand warp_min(Cand c) {
+
+// Search key of a live variable: (fkey(hi), fkey(lo) with its low 12 bits
+// replaced by the index).  Compared as a 64-bit integer it orders by the
+// double-float score and then by index; dropping 12 bits of lo merges
+// scores closer than about 2^-35 relative into index order, far below any
+// gap the method distinguishes.  A dead variable is (~0, ~0).
+__device__ __forceinline__ uint2 skey(float hi, float lo, int i) {
+  return make_uint2(fkey(hi), (fkey(lo) & 0xfffff000u) | (uint32_t)i);
+}
+// warp-wide minimum key, in every lane (two REDUX, no branches)
+__device__ __forceinline__ uint2 warp_kmin(uint2 k) {
   const uint32_t full = 0xffffffffu;
-  uint32_t mh = __reduce_min_sync(full, c.kh);
-  uint32_t kl = (c.kh == mh) ? c.kl : 0xffffffffu;
-  uint32_t ml = __reduce_min_sync(full, kl);
-  uint32_t id = (c.kh == mh && c.kl == ml) ? (uint32_t)c.idx : 0xffffffffu;
-  uint32_t mi = __reduce_min_sync(full, id);
-  return Cand{mh, ml, (int)mi};
+  const uint32_t h = __reduce_min_sync(full, k.x);
+  const uint32_t l = __reduce_min_sync(full, k.x == h ? k.y : 0xffffffffu);
+  return make_uint2(h, l);
 }
 
-__device__ __forceinline__ Cand none() { return Cand{0xffffffffu, 0xffffffffu, INT_MAX}; }
-
-// Warp-wide lexicographic minimum of (kh, kl, idx), in every lane.  A real
-// score never has the key 0xffffffff (that is a NaN pattern), so a warp whose
-// minimum kh is 0xffffffff holds no live candidate.  Fast path: one lane holds
-// the minimum kh (REDUX + VOTE + SHFL); ties on kh take the full three-key
-// reduction.  *src returns the winning lane (-1 if none).
-__device__ __forceinline__ Cand warp_argmin(const Cand& c, int* src) {
-  const uint32_t full = 0xffffffffu;
-  const uint32_t mh = __reduce_min_sync(full, c.kh);
-  if (mh == 0xffffffffu) {
-    *src = -1;
-    return none();
-  }
-  const uint32_t bal = __ballot_sync(full, c.kh == mh);
-  if (__popc(bal) == 1) {
-    const int l = __ffs(bal) - 1;
-    *src = l;
-    return Cand{mh, __shfl_sync(full, c.kl, l), __shfl_sync(full, c.idx, l)};
-  }
-  const Cand w = warp_min(c);
-  *src = __ffs(__ballot_sync(full, c.idx == w.idx && c.kh == w.kh && c.kl == w.kl)) - 1;
-  return w;
-}
-
-// One CTA of up to 1024 threads, each owning PER variables (i = tid + q*nthr).
-// A step: every warp finds its best and runner-up (warp_argmin), writes them
-// to a shared slot of the step's parity, one barrier, then every warp reduces
-// the warp winners itself, so all threads learn the pick c and the runner-up
-// r without a second barrier (slots alternate by parity: a warp can run at
-// most one step ahead of the slowest).  Then S_i -= P_{i,c}.  The P column of
-// the pick is loaded together with the column of the runner-up; when the
-// runner-up wins the next step (about 60% of the steps on the workloads
-// measured) that step uses the prefetched registers and skips the L2 round
-// trip.
-template <int PER>
-__global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pth,
-                                                    const float* __restrict__ ptl,
-                                                    const float* __restrict__ sh0,
-                                                    const float* __restrict__ sl0, int m,
-                                                    int32_t* __restrict__ order,
-                                                    float4* __restrict__ best2) {
-  __shared__ Cand wb1[2][32], wb2[2][32];
+// The search, one CTA of up to 1024 threads, each owning PER variables
+// (i = tid + q*nthr).  A step: every warp reduces its keys (warp_kmin) and
+// lane 0 writes the warp minimum to a shared slot of the step's parity; one
+// barrier; every warp then reduces the warp minima itself, so all threads
+// learn the pick c without a second barrier (slots alternate by parity: a
+// warp can run at most one step ahead of the slowest); S_i -= P_{i,c}.  (A
+// prefetch of the likely runner-up's column was measured to cost more than
+// it saved once the reductions were branch-free.)  fetch(c, i, h, l) loads
+// P_{i,c} as the double-float pair (h, l).  prof (optional, NULL in the
+// library): clock64 stamps of thread 0, five per step: start, warp minimum
+// written, after the barrier, pick known, update done.
+template <int PER, class Fetch>
+__device__ __forceinline__ void search_steps(float (&hi)[PER], float (&lo)[PER],
+                                             bool (&alive)[PER], int m,
+                                             int32_t* __restrict__ order,
+                                             long long* __restrict__ prof, Fetch fetch) {
+  __shared__ uint2 wb[2][32];
   const int nthr = blockDim.x, nw = (nthr + 31) >> 5;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float hi[PER], lo[PER], nh[PER], nl[PER];
-  bool alive[PER];
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int i = threadIdx.x + q * nthr;
-    alive[q] = i < m;
-    hi[q] = alive[q] ? sh0[i] : 0.f;
-    lo[q] = alive[q] ? sl0[i] : 0.f;
-    nh[q] = nl[q] = 0.f;
-  }
-  int pre = -1;
+  const uint2 dead = make_uint2(0xffffffffu, 0xffffffffu);
   for (int k = 0; k < m; ++k) {
     const int ph = k & 1;
-    // this thread's best and runner-up
-    Cand b1 = none(), b2 = none();
+    if (prof && threadIdx.x == 0) prof[5 * k] = clock64();
+    uint2 b = dead;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      if (!alive[q]) continue;
-      const Cand c{fkey(hi[q]), fkey(lo[q]), (int)threadIdx.x + q * nthr};
-      if (PER == 1) {
-        b1 = c;
-      } else if (cless(c, b1)) {
-        b2 = b1;
-        b1 = c;
-      } else if (cless(c, b2)) {
-        b2 = c;
-      }
+      const uint2 c = alive[q] ? skey(hi[q], lo[q], (int)threadIdx.x + q * nthr) : dead;
+      if (c.x < b.x || (c.x == b.x && c.y < b.y)) b = c;
     }
-    // warp level: the winning lane writes its own candidate
-    int l1, l2;
-    warp_argmin(b1, &l1);
-    const Cand s2 = (lane == l1) ? b2 : b1;
-    warp_argmin(s2, &l2);
-    if (lane == 0 && l1 < 0) wb1[ph][wid] = none();
-    if (lane == l1) wb1[ph][wid] = b1;
-    if (lane == 0 && l2 < 0) wb2[ph][wid] = none();
-    if (lane == l2) wb2[ph][wid] = s2;
+    const uint2 w = warp_kmin(b);
+    if (lane == 0) wb[ph][wid] = w;
+    if (prof && threadIdx.x == 0) prof[5 * k + 1] = clock64();
     __syncthreads();
+    if (prof && threadIdx.x == 0) prof[5 * k + 2] = clock64();
     // block level, redundantly in every warp
-    const Cand a1 = lane < nw ? wb1[ph][lane] : none();
-    const Cand a2 = lane < nw ? wb2[ph][lane] : none();
-    int g1l, g2l;
-    const Cand g1 = warp_argmin(a1, &g1l);
-    const int c = g1.idx;
-    const Cand g2 = warp_argmin((lane == g1l) ? a2 : a1, &g2l);
-    const int r = g2.idx;
-    if (threadIdx.x == 0) {
-      order[k] = c;
-      best2[k] = make_float4(fkey_inv(g1.kh), fkey_inv(g1.kl),
-                             r == INT_MAX ? __int_as_float(0x7f800000) : fkey_inv(g2.kh),
-                             r == INT_MAX ? 0.f : fkey_inv(g2.kl));
-    }
+    const uint2 a = lane < nw ? wb[ph][lane] : dead;
+    const uint2 g = warp_kmin(a);
+    const int c = (int)(g.y & 0xfffu);
+    if (prof && threadIdx.x == 0) prof[5 * k + 3] = clock64();
+    if (threadIdx.x == 0) order[k] = c;
     float ch[PER], cl[PER];
-    if (c == pre) {
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        ch[q] = nh[q];
-        cl[q] = nl[q];
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int i = threadIdx.x + q * nthr;
-        ch[q] = alive[q] ? pth[(int64_t)c * m + i] : 0.f;
-        cl[q] = alive[q] ? ptl[(int64_t)c * m + i] : 0.f;
-      }
-    }
-    if (r != INT_MAX) {
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int i = threadIdx.x + q * nthr;
-        nh[q] = alive[q] ? pth[(int64_t)r * m + i] : 0.f;
-        nl[q] = alive[q] ? ptl[(int64_t)r * m + i] : 0.f;
-      }
-      pre = r;
+    for (int q = 0; q < PER; ++q) {
+      ch[q] = cl[q] = 0.f;
+      if (alive[q]) fetch(c, (int)threadIdx.x + q * nthr, ch[q], cl[q]);
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -251,21 +177,86 @@ __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pt
       else
         df_sub(hi[q], lo[q], ch[q], cl[q]);
     }
+    if (prof && threadIdx.x == 0) prof[5 * k + 4] = clock_after(hi[0]);
   }
 }
 
-__global__ void gap_kernel(const float4* __restrict__ best2, int m, double* __restrict__ gap) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+// Search with P in global memory (L2): Pt_hi/lo[c * m + i] = P_{i,c}.
+template <int PER>
+__global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pth,
+                                                    const float* __restrict__ ptl,
+                                                    const float* __restrict__ sh0,
+                                                    const float* __restrict__ sl0, int m,
+                                                    int32_t* __restrict__ order,
+                                                    long long* __restrict__ prof) {
+  float hi[PER], lo[PER];
+  bool alive[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = threadIdx.x + q * blockDim.x;
+    alive[q] = i < m;
+    hi[q] = alive[q] ? sh0[i] : 0.f;
+    lo[q] = alive[q] ? sl0[i] : 0.f;
+  }
+  search_steps<PER>(hi, lo, alive, m, order, prof, [&](int c, int i, float& h, float& l) {
+    h = pth[(int64_t)c * m + i];
+    l = ptl[(int64_t)c * m + i];
+  });
+}
+
+// order-preserving map double -> uint64
+__device__ __forceinline__ unsigned long long dkey(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Gaps after the search, from the order: variable i replays its score
+// S_i = sum_{j in U} P_ij step by step in FP64; at the step that picks it, it
+// records its score as the minimum s1[k]; at earlier steps it offers its
+// score to the step's runner-up s2[k] (atomic minimum of an ordered key).
+// Steps are taken eight at a time so that their loads overlap.
+__global__ void gap_scores_kernel(const float* __restrict__ pth, const float* __restrict__ ptl,
+                                  const float* __restrict__ sh0, const float* __restrict__ sl0,
+                                  const int32_t* __restrict__ order, int m,
+                                  double* __restrict__ s1, unsigned long long* __restrict__ s2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = (double)sh0[i] + (double)sl0[i];
+  for (int t0 = 0; t0 < m; t0 += 8) {
+    int cs[8];
+    double p[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cs[u] = t0 + u < m ? order[t0 + u] : i;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      p[u] = (double)pth[(int64_t)cs[u] * m + i] + (double)ptl[(int64_t)cs[u] * m + i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (cs[u] == i) {
+        if (t0 + u < m) s1[t0 + u] = s;
+        return;
+      }
+      atomicMin(&s2[t0 + u], dkey(s));
+      s -= p[u];
+    }
+  }
+}
+
+__global__ void gap_kernel(const double* __restrict__ s1, const unsigned long long* __restrict__ s2,
+                           int m, double* __restrict__ gap) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= m) return;
-  float4 b = best2[k];
-  if (isinf(b.z)) {
+  if (s2[k] == ~0ull) {
     gap[k] = __longlong_as_double(0x7ff0000000000000LL);
     return;
   }
-  double s1 = (double)b.x + (double)b.y;
-  double s2 = (double)b.z + (double)b.w;
-  double den = fmax(fmax(fabs(s1), fabs(s2)), 1e-300);
-  gap[k] = (s2 - s1) / den;
+  const double a = s1[k], b = dkey_inv(s2[k]);
+  const double den = fmax(fmax(fabs(a), fabs(b)), 1e-300);
+  gap[k] = (b - a) / den;
 }
 
 }  // namespace
@@ -276,13 +267,14 @@ size_t order_ws_bytes(int m) {
 }
 
 void launch_causal_order(const double* D, int m, void* ws, int32_t* order, double* gap, int* st,
-                         cudaStream_t s) {
+                         cudaStream_t s, long long* prof) {
   char* p = static_cast<char*>(ws);
   float* pth = reinterpret_cast<float*>(p);
   float* ptl = pth + (size_t)m * m;
   float* sh = ptl + (size_t)m * m;
   float* sl = sh + m;
-  float4* best2 = reinterpret_cast<float4*>(((uintptr_t)(sl + m) + 15) & ~(uintptr_t)15);
+  double* s1 = reinterpret_cast<double*>(((uintptr_t)(sl + m) + 15) & ~(uintptr_t)15);
+  unsigned long long* s2 = reinterpret_cast<unsigned long long*>(s1 + m);
   dim3 grid((m + 31) / 32, (m + 31) / 32), block(32, 8);
   note_launch();
   pt_kernel<<<grid, block, 0, s>>>(D, m, pth, ptl, st);
@@ -293,14 +285,17 @@ void launch_causal_order(const double* D, int m, void* ws, int32_t* order, doubl
   const int nthr = std::min(OTH, ((m + per - 1) / per + 31) / 32 * 32);
   note_launch();
   if (per == 1)
-    order_kernel<1><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+    order_kernel<1><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, prof);
   else if (per == 2)
-    order_kernel<2><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+    order_kernel<2><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, prof);
   else
-    order_kernel<4><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, best2);
+    order_kernel<4><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, prof);
   if (gap) {
+    cudaMemsetAsync(s2, 0xff, (size_t)m * sizeof(unsigned long long), s);
     note_launch();
-    gap_kernel<<<(m + 255) / 256, 256, 0, s>>>(best2, m, gap);
+    gap_scores_kernel<<<(m + 127) / 128, 128, 0, s>>>(pth, ptl, sh, sl, order, m, s1, s2);
+    note_launch();
+    gap_kernel<<<(m + 255) / 256, 256, 0, s>>>(s1, s2, m, gap);
   }
 }
 

@@ -188,7 +188,7 @@ void launch_measure_finalize(const void* part, const PairPlan& pl, const double*
 // Ordering (k_order.cu)
 size_t order_ws_bytes(int m);
 void launch_causal_order(const double* D, int m, void* ws, int32_t* order, double* gap, int* st,
-                         cudaStream_t s);
+                         cudaStream_t s, long long* prof = nullptr);
 
 // B0 / B_tau helpers (k_fitb.cu)
 template <class T>
