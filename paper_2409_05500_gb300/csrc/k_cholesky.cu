@@ -3,18 +3,25 @@
 // and the causally ordered residual covariance whose factor gives B0 (Sec. 4.2
 // item 5) are both factored here on the mixed-precision path.
 //
-// GB300 design.  n <= 512 is far too small to fill the GPU, and one CTA
-// alone spends most of its time on the trailing updates, so the factorisation
-// runs on a cluster of up to 8 CTAs (one per SM) that keep the whole matrix in
-// their shared memory: the 32-wide block columns are dealt round-robin to the
-// CTAs.  Block column k is factored by its owner (diagonal block by one warp,
-// its inverse, then the panel below it); the other CTAs read the finished
-// panel straight out of the owner's shared memory (distributed shared memory)
-// and apply it to their own block columns.  One hardware cluster barrier per
-// block column orders the two.  Look-ahead: the owner of block column k + 1
-// applies panel k to that column first, factors it and signals, and only then
-// applies panel k to its other columns, so the serial chain per block column
-// is: copy panel, update one block column, factor 32 x 32, invert, panel.
+// GB300 design.  n <= 512 is far too small to fill the GPU and one CTA alone
+// spends most of its time in the trailing updates, so the factorisation runs
+// on a cluster of up to 8 CTAs (one per SM) that keep the whole lower
+// triangle in their shared memory, dealt out by 32-row blocks round-robin:
+// CTA t owns row blocks R_b with b = t (mod cl), columns 0 .. 32(b+1)-1.
+// Step k (block column C_k):
+//   - the owner of R_k has factored the diagonal block A[R_k][C_k] and
+//     inverted it (one warp, registers and shared-memory broadcasts);
+//   - every CTA copies that 32 x 32 inverse out of the owner's shared memory
+//     (distributed shared memory) and forms the panel rows of its own row
+//     blocks, L[R_b][C_k] = A[R_b][C_k] Linv^T, in place;
+//   - the trailing update A[R_b][C_j] -= L[R_b][C_k] L[R_j][C_k]^T needs the
+//     panel rows of every row block j <= b: they are gathered from their
+//     owners at the start of step k + 1.
+// Look-ahead: the owner of R_{k+1} applies panel k to its diagonal block
+// right after forming its own panel rows and factors it, so the chain from
+// one diagonal block to the next is: copy inverse, a few 32 x 32 products,
+// factor and invert 32 x 32.  Updates that no one waits for run after the
+// CTA has signalled the step (split cluster barrier arrive / wait).
 //
 // Outputs follow the multi-kernel path: L in the lower triangle of A (the
 // strict upper triangle is left as it was) and, per 64-block of rows, the
@@ -34,10 +41,6 @@ constexpr int RS = CB + 4;    // shared row stride: 16-byte rows, conflict-free 
 constexpr int CL_MAX = 8;     // CTAs per cluster (portable maximum)
 constexpr int CTH = 512;      // threads per CTA
 constexpr int CL_NMAX = 512;  // largest n handled
-#ifndef VL_CHOL_RB
-#define VL_CHOL_RB 4
-#endif
-constexpr int RB = VL_CHOL_RB;  // rows per warp pass in the panel and update
 
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
@@ -76,48 +79,56 @@ __device__ __forceinline__ float4 ld_cluster4(unsigned addr) {
 }
 
 // Shared-memory layout of one CTA (floats):
-//   own   owned block columns, each rows k0 .. n-1 of 32 columns (stride RS)
-//   pbuf  copy of the current panel, rows (k+1)*32 .. n-1 (stride RS)
+//   own   owned row blocks: R_b as 32 rows x ldb(b) = 32(b+1) + 4 floats
+//         (columns 0 .. 32(b+1)-1; the 4-float pad makes a lane-per-row
+//         float4 read conflict-free)
+//   gbuf  gathered panel rows of the previous block column, rows 32k .. n-1
+//         of step k (stride RS)
 //   li    32 x 32 inverses of the owned diagonal blocks (stride RS)
-//   scr   64 rows of scratch: the diagonal factor's columns, then its rows;
-//         the partner inverse and B A^{-1} when combining 64-blocks
+//   lcur  copy of the current diagonal inverse (stride RS)
+//   scr   64 rows of scratch for the diagonal factor and the 64-block combine
 struct Layout {
   int n, nblk, cl, rank;
-  // offset (in rows) of owned block b inside `own`
-  __host__ __device__ int own_row0(int b) const {
-    int r = 0;
-    for (int c = rank; c < b; c += cl) r += n - c * CB;
-    return r;
+  __host__ __device__ static int ldb(int b) { return CB * (b + 1) + 4; }
+  __host__ __device__ int owner(int b) const { return b % cl; }
+  // offset (floats) of owned row block b inside `own`
+  __host__ __device__ int own_off(int b) const {
+    int o = 0;
+    for (int c = rank; c < b; c += cl) o += CB * ldb(c);
+    return o;
   }
-  __host__ __device__ int own_rows() const {
-    int r = 0;
-    for (int c = rank; c < nblk; c += cl) r += n - c * CB;
-    return r;
+  __host__ __device__ int own_floats() const {
+    int o = 0;
+    for (int c = rank; c < nblk; c += cl) o += CB * ldb(c);
+    return o;
   }
   __host__ __device__ int n_owned() const { return nblk > rank ? (nblk - 1 - rank) / cl + 1 : 0; }
+  __host__ __device__ int gbuf_off() const { return own_floats(); }
+  __host__ __device__ int li_off() const { return gbuf_off() + (n > CB ? n - CB : 0) * RS; }
+  __host__ __device__ int lcur_off() const { return li_off() + n_owned() * CB * RS; }
+  __host__ __device__ int scr_off() const { return lcur_off() + CB * RS; }
+  __host__ __device__ int total() const { return scr_off() + 2 * CB * RS; }
 };
 
-// rows of shared memory (each RS floats): own, pbuf, li, scr (64 rows)
 inline size_t cluster_chol_smem(int n, int cl, int rank) {
   Layout L{n, (n + CB - 1) / CB, cl, rank};
-  const size_t rows = (size_t)L.own_rows() + std::max(0, n - CB) + (size_t)L.n_owned() * CB + 2 * CB;
-  return rows * RS * sizeof(float);
+  return (size_t)L.total() * sizeof(float);
 }
 
-// Warp 0: factor the diagonal block (rows of `blk`, nb valid rows/columns;
-// identity padding beyond nb) in place; its rows also go to scr.  Lane r
+// Warp 0: factor the diagonal block (rows of `blk`, stride ldb, nb valid
+// rows/columns; identity padding beyond nb) in place; its rows also go to scr.  Lane r
 // holds row r in registers; column j of the factor is published through
 // shared memory (scr row j) and read back as float4 broadcasts for the rank-1
 // update of the remaining columns.  Returns true if a pivot failed the
 // relative threshold.
-__device__ __noinline__ bool factor_diag(float* blk, int nb, const double* diag0k,
+__device__ __noinline__ bool factor_diag(float* blk, int ldb, int nb, const double* diag0k,
                                          float rel_tol, float* scr) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   float a[CB];
 #pragma unroll
   for (int c4 = 0; c4 < CB; c4 += 4) {
-    const float4 v = lane < nb ? *reinterpret_cast<const float4*>(blk + lane * RS + c4)
+    const float4 v = lane < nb ? *reinterpret_cast<const float4*>(blk + lane * ldb + c4)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     a[c4] = v.x;
     a[c4 + 1] = v.y;
@@ -160,7 +171,7 @@ __device__ __noinline__ bool factor_diag(float* blk, int nb, const double* diag0
     const float4 v = make_float4(c4 <= lane ? a[c4] : 0.f, c4 + 1 <= lane ? a[c4 + 1] : 0.f,
                                  c4 + 2 <= lane ? a[c4 + 2] : 0.f, c4 + 3 <= lane ? a[c4 + 3] : 0.f);
     *reinterpret_cast<float4*>(scr + lane * RS + c4) = v;
-    if (lane < nb) *reinterpret_cast<float4*>(blk + lane * RS + c4) = v;
+    if (lane < nb) *reinterpret_cast<float4*>(blk + lane * ldb + c4) = v;
   }
   __syncwarp();
   return __any_sync(full, lbad);
@@ -191,26 +202,66 @@ __device__ __noinline__ void invert_diag(const float* scr, float* li) {
   for (int r = 0; r < CB; ++r) li[r * RS + lane] = x[r];
 }
 
-// All warps: panel rows below the diagonal block of block column b,
-// P[i][c] = sum_{q <= c} A[i][q] Linv[c][q], in place (rows 32 .. rows-1 of blk).
-__device__ __forceinline__ void panel_rows(float* blk, int rows, const float* li) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float lr[CB];  // row `lane` of Linv
+// One warp: rows [r0, r1) of a 32-row tile, out[r][c] -= sum_q P[r][q] Q[c][q]
+// for lane c; Q rows c >= qrows count as zero.  P rows are read as float4
+// broadcasts, Q row c by lane c (stride ldq, conflict-free for ldq = 4 mod 32).
+__device__ __noinline__ void tile_rows(float* out, int ldo, const float* P, int ldp,
+                                          const float* Q, int ldq, int qrows, int r0, int r1) {
+  const int lane = threadIdx.x & 31;
+  float q[CB];
+  {
+    const bool ok = lane < qrows;
+    const float* row = Q + (size_t)(ok ? lane : 0) * ldq;
+#pragma unroll
+    for (int q4 = 0; q4 < CB; q4 += 4) {
+      const float4 v = ok ? *reinterpret_cast<const float4*>(row + q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      q[q4] = v.x;
+      q[q4 + 1] = v.y;
+      q[q4 + 2] = v.z;
+      q[q4 + 3] = v.w;
+    }
+  }
+  for (int r = r0; r < r1; r += 4) {
+    float old[4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) old[u] = out[(size_t)min(r + u, r1 - 1) * ldo + lane];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float* prow = P + (size_t)min(r + u, r1 - 1) * ldp;
+#pragma unroll
+      for (int q4 = 0; q4 < CB; q4 += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(prow + q4);
+        acc[u] = fmaf(v.x, q[q4], acc[u]);
+        acc[u] = fmaf(v.y, q[q4 + 1], acc[u]);
+        acc[u] = fmaf(v.z, q[q4 + 2], acc[u]);
+        acc[u] = fmaf(v.w, q[q4 + 3], acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r + u < r1) out[(size_t)(r + u) * ldo + lane] = old[u] - acc[u];
+  }
+}
+
+// One warp: panel rows [r0, r1), X[r][c] = sum_{q <= c} X[r][q] Linv[c][q] in
+// place (lane c; Linv lower triangular, stride RS).
+__device__ __noinline__ void panel_tile_rows(float* X, int ldx, const float* linv, int r0,
+                                                int r1) {
+  const int lane = threadIdx.x & 31;
+  float lr[CB];
 #pragma unroll
   for (int q4 = 0; q4 < CB; q4 += 4) {
-    const float4 v = *reinterpret_cast<const float4*>(li + lane * RS + q4);
+    const float4 v = *reinterpret_cast<const float4*>(linv + lane * RS + q4);
     lr[q4] = v.x;
     lr[q4 + 1] = v.y;
     lr[q4 + 2] = v.z;
     lr[q4 + 3] = v.w;
   }
-  for (int i0 = CB + RB * warp; i0 < rows; i0 += RB * (CTH / 32)) {
-    float acc[RB];
+  for (int r = r0; r < r1; r += 4) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int u = 0; u < RB; ++u) acc[u] = 0.f;
-#pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const float* row = blk + (size_t)min(i0 + u, rows - 1) * RS;
+    for (int u = 0; u < 4; ++u) {
+      const float* row = X + (size_t)min(r + u, r1 - 1) * ldx;
 #pragma unroll
       for (int q4 = 0; q4 < CB; q4 += 4) {
         const float4 v = *reinterpret_cast<const float4*>(row + q4);
@@ -222,140 +273,92 @@ __device__ __forceinline__ void panel_rows(float* blk, int rows, const float* li
     }
     __syncwarp();
 #pragma unroll
-    for (int u = 0; u < RB; ++u)
-      if (i0 + u < rows) blk[(size_t)(i0 + u) * RS + lane] = acc[u];
-  }
-}
-
-// All warps: block column j (rows j0 .. n-1 in blk) minus the panel product,
-// A_j[i][c] -= sum_q P[i][q] P[j0 + c][q]; panel row i is P + (i - prow0) * RS.
-__device__ __noinline__ void update_block(float* blk, int j0, int n, const float* P,
-                                             int prow0) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float pj[CB];
-  {
-    const bool ok = j0 + lane < n;
-    const float* row = P + (size_t)(min(j0 + lane, n - 1) - prow0) * RS;
-#pragma unroll
-    for (int q4 = 0; q4 < CB; q4 += 4) {
-      const float4 v = ok ? *reinterpret_cast<const float4*>(row + q4)
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-      pj[q4] = v.x;
-      pj[q4 + 1] = v.y;
-      pj[q4 + 2] = v.z;
-      pj[q4 + 3] = v.w;
-    }
-  }
-  const int rows = n - j0;
-  for (int i0 = RB * warp; i0 < rows; i0 += RB * (CTH / 32)) {
-    float old[RB], acc[RB];
-#pragma unroll
-    for (int u = 0; u < RB; ++u) acc[u] = 0.f;
-#pragma unroll
-    for (int u = 0; u < RB; ++u) old[u] = blk[(size_t)min(i0 + u, rows - 1) * RS + lane];
-#pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const float* row = P + (size_t)(j0 + min(i0 + u, rows - 1) - prow0) * RS;
-#pragma unroll
-      for (int q4 = 0; q4 < CB; q4 += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(row + q4);
-        acc[u] = fmaf(v.x, pj[q4], acc[u]);
-        acc[u] = fmaf(v.y, pj[q4 + 1], acc[u]);
-        acc[u] = fmaf(v.z, pj[q4 + 2], acc[u]);
-        acc[u] = fmaf(v.w, pj[q4 + 3], acc[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < RB; ++u)
-      if (i0 + u < rows) blk[(size_t)(i0 + u) * RS + lane] = old[u] - acc[u];
-  }
-}
-
-// Factor block column b owned by this CTA: warp 0 factors and inverts the
-// diagonal block, then all warps form the panel below it.
-__device__ __noinline__ void factor_block(const Layout& L, float* own, float* li_all,
-                                          float* scr, int b, const double* diag0,
-                                          float rel_tol, int* bad, unsigned long long* pf) {
-  const int k0 = b * CB, nb = min(CB, L.n - k0);
-  float* blk = own + (size_t)L.own_row0(b) * RS;
-  float* li = li_all + (size_t)((b - L.rank) / L.cl) * CB * RS;
-  if ((threadIdx.x >> 5) == 0) {
-    const bool fail = factor_diag(blk, nb, diag0 + k0, rel_tol, scr);
-    if (fail && (threadIdx.x & 31) == 0) *bad = 1;
-    if (pf && threadIdx.x == 0) pf[0] = gtime();
-    invert_diag(scr, li);
-    if (pf && threadIdx.x == 0) pf[1] = gtime();
-  }
-  __syncthreads();
-  panel_rows(blk, L.n - k0, li);
-  __syncthreads();
-  if (pf && threadIdx.x == 0) pf[2] = gtime();
-}
-
-// Warp 0 of the owner of an even block column b: lower-left quadrant
-// -C^{-1} (B A^{-1}) of the 64 x 64 inverse (C^{-1} = I and a zero quadrant
-// when b has no partner).  A^{-1} and B are local, C^{-1} is copied from the
-// partner's shared memory.
-__device__ __noinline__ void combine_64(const Layout& L, const float* own, float* li_all,
-                                        float* scr, int b, float* out) {
-  const int lane = threadIdx.x & 31, n = L.n, nblk = L.nblk, cl = L.cl, rank = L.rank;
-  const int k0 = b * CB;
-  const float* li = li_all + (size_t)((b - rank) / cl) * CB * RS;
-  float x[CB];
-  if (b + 1 < nblk) {
-    const int pr = (b + 1) % cl;
-    const Layout Lp{n, nblk, cl, pr};
-    const size_t li_row = (size_t)Lp.own_rows() + max(0, n - CB) + (size_t)((b + 1 - pr) / cl) * CB;
-    const unsigned src = map_rank(own, pr) + (unsigned)(li_row * RS * sizeof(float));
-    float* ci = scr;  // partner inverse C^{-1}
-#pragma unroll
-    for (int q4 = 0; q4 < CB; q4 += 4)
-      *reinterpret_cast<float4*>(ci + lane * RS + q4) =
-          ld_cluster4(src + (unsigned)((lane * RS + q4) * sizeof(float)));
-    // t = B A^{-1}, row `lane`: B[lane][q] = L[k0 + 32 + lane][k0 + q]
-    const bool okr = k0 + CB + lane < n;
-    const float* brow = own + ((size_t)L.own_row0(b) + CB + (okr ? lane : 0)) * RS;
-    float t[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) t[c] = 0.f;
-#pragma unroll
-    for (int q = 0; q < CB; ++q) {
-      const float bq = okr ? brow[q] : 0.f;
-#pragma unroll
-      for (int c4 = 0; c4 < CB; c4 += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(li + q * RS + c4);
-        t[c4] = fmaf(bq, v.x, t[c4]);
-        t[c4 + 1] = fmaf(bq, v.y, t[c4 + 1]);
-        t[c4 + 2] = fmaf(bq, v.z, t[c4 + 2]);
-        t[c4 + 3] = fmaf(bq, v.w, t[c4 + 3]);
-      }
-    }
-    float* tb = scr + CB * RS;
-#pragma unroll
-    for (int c4 = 0; c4 < CB; c4 += 4)
-      *reinterpret_cast<float4*>(tb + lane * RS + c4) = make_float4(t[c4], t[c4 + 1], t[c4 + 2], t[c4 + 3]);
+    for (int u = 0; u < 4; ++u)
+      if (r + u < r1) X[(size_t)(r + u) * ldx + lane] = acc[u];
     __syncwarp();
-    // x = -C^{-1} t, row `lane`
+  }
+}
+
+// Copy rows [g0, g1) of block column kc (panel rows, 32 floats each) from
+// their owners' shared memory into gbuf (row g at (g - gbase) * RS).
+__device__ __forceinline__ void gather_rows(const Layout& L, const float* smem_base, float* gbuf,
+                                            int gbase, int kc, int g0, int g1) {
+  const int tot = (g1 - g0) * (CB / 4);
+  for (int base = threadIdx.x; base < tot; base += 4 * CTH) {
+    float4 v[4];
 #pragma unroll
-    for (int c = 0; c < CB; ++c) x[c] = 0.f;
-#pragma unroll
-    for (int q = 0; q < CB; ++q) {
-      const float cq = ci[lane * RS + q];
-#pragma unroll
-      for (int c4 = 0; c4 < CB; c4 += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(tb + q * RS + c4);
-        x[c4] = fmaf(-cq, v.x, x[c4]);
-        x[c4 + 1] = fmaf(-cq, v.y, x[c4 + 1]);
-        x[c4 + 2] = fmaf(-cq, v.z, x[c4 + 2]);
-        x[c4 + 3] = fmaf(-cq, v.w, x[c4 + 3]);
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * CTH;
+      if (idx < tot) {
+        const int g = g0 + (idx >> 3), rb = g / CB, o = L.owner(rb);
+        const Layout Lo{L.n, L.nblk, L.cl, o};
+        const size_t off = (size_t)Lo.own_off(rb) + (size_t)(g - rb * CB) * Layout::ldb(rb) +
+                           (size_t)kc * CB + (idx & 7) * 4;
+        v[u] = ld_cluster4(map_rank(smem_base + off, o));
       }
     }
-  } else {
-    // no partner: C^{-1} = I, lower-left quadrant zero
 #pragma unroll
-    for (int c = 0; c < CB; ++c) {
-      out[(CB + lane) * CHOL_NB + CB + c] = (c == lane) ? 1.f : 0.f;
-      x[c] = 0.f;
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * CTH;
+      if (idx < tot)
+        *reinterpret_cast<float4*>(gbuf + (size_t)(g0 + (idx >> 3) - gbase) * RS + (idx & 7) * 4) = v[u];
+    }
+  }
+}
+
+// Warp 0 of the owner of an odd row block b: lower-left quadrant
+// -C^{-1} (B A^{-1}) of the 64 x 64 inverse for row blocks b-1, b.  B (its
+// panel rows of block column b-1) and C^{-1} are local; A^{-1} is copied from
+// the owner of b-1.
+__device__ __noinline__ void combine_64(const Layout& L, const float* smem_base, const float* Xb,
+                                        int ldxb, const float* cinv, float* scr, int b,
+                                        float* out) {
+  const int lane = threadIdx.x & 31;
+  const int o = L.owner(b - 1);
+  const Layout Lo{L.n, L.nblk, L.cl, o};
+  const size_t off = (size_t)Lo.li_off() + (size_t)((b - 1 - o) / L.cl) * CB * RS;
+  float* ai = scr;  // A^{-1}
+#pragma unroll
+  for (int q4 = 0; q4 < CB; q4 += 4)
+    *reinterpret_cast<float4*>(ai + lane * RS + q4) =
+        ld_cluster4(map_rank(smem_base + off + lane * RS + q4, o));
+  __syncwarp();
+  // t = B A^{-1}, row `lane` (rows beyond n are zero in shared memory)
+  const float* brow = Xb + (size_t)lane * ldxb + (b - 1) * CB;
+  float t[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) t[c] = 0.f;
+#pragma unroll
+  for (int q = 0; q < CB; ++q) {
+    const float bq = brow[q];
+#pragma unroll
+    for (int c4 = 0; c4 < CB; c4 += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(ai + q * RS + c4);
+      t[c4] = fmaf(bq, v.x, t[c4]);
+      t[c4 + 1] = fmaf(bq, v.y, t[c4 + 1]);
+      t[c4 + 2] = fmaf(bq, v.z, t[c4 + 2]);
+      t[c4 + 3] = fmaf(bq, v.w, t[c4 + 3]);
+    }
+  }
+  float* tb = scr + CB * RS;
+#pragma unroll
+  for (int c4 = 0; c4 < CB; c4 += 4)
+    *reinterpret_cast<float4*>(tb + lane * RS + c4) = make_float4(t[c4], t[c4 + 1], t[c4 + 2], t[c4 + 3]);
+  __syncwarp();
+  // x = -C^{-1} t, row `lane`
+  float x[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) x[c] = 0.f;
+#pragma unroll
+  for (int q = 0; q < CB; ++q) {
+    const float cq = cinv[lane * RS + q];
+#pragma unroll
+    for (int c4 = 0; c4 < CB; c4 += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(tb + q * RS + c4);
+      x[c4] = fmaf(-cq, v.x, x[c4]);
+      x[c4 + 1] = fmaf(-cq, v.y, x[c4 + 1]);
+      x[c4 + 2] = fmaf(-cq, v.z, x[c4 + 2]);
+      x[c4 + 3] = fmaf(-cq, v.w, x[c4 + 3]);
     }
   }
 #pragma unroll
@@ -363,6 +366,10 @@ __device__ __noinline__ void combine_64(const Layout& L, const float* own, float
 }
 
 // One cluster of cl = min(8, ceil(n/32)) CTAs factors A (n <= 512) in place.
+// prof (optional, NULL in the library): globaltimer stamps, 8 per CTA and
+// step: wait done, first rows gathered, priority updates, panel rows,
+// look-ahead update, diagonal factored and inverted, end of the step,
+// diagonal factored (before its inverse).
 __global__ void __launch_bounds__(CTH, 1)
     chol_cluster_kernel(float* __restrict__ A, int64_t lda, int n, float* __restrict__ dinv,
                         const double* __restrict__ diag0, float rel_tol, int* st,
@@ -372,112 +379,168 @@ __global__ void __launch_bounds__(CTH, 1)
   const Layout L{n, nblk, (int)cluster_size(), (int)cluster_rank()};
   const int rank = L.rank, cl = L.cl;
   float* own = cc_smem;
-  float* pbuf = own + (size_t)L.own_rows() * RS;
-  float* li_all = pbuf + (size_t)max(0, n - CB) * RS;
-  float* scr = li_all + (size_t)L.n_owned() * CB * RS;
+  float* gbuf = cc_smem + L.gbuf_off();
+  float* li_all = cc_smem + L.li_off();
+  float* lcur = cc_smem + L.lcur_off();
+  float* scr = cc_smem + L.scr_off();
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, nwarp = CTH / 32;
   if (tid == 0) bad = 0;
-  // owned block columns from global memory (rows k0 .. n-1; columns >= n read as 0)
+  unsigned long long* pf = prof ? prof + (size_t)rank * nblk * 8 : nullptr;
+  auto blk = [&](int b) { return own + L.own_off(b); };
+  auto nbr = [&](int b) { return min(CB, n - b * CB); };
+  auto lib = [&](int b) { return li_all + (size_t)((b - rank) / cl) * CB * RS; };
+  auto first_after = [&](int k) {  // first owned row block > k
+    int b = rank;
+    while (b <= k) b += cl;
+    return b;
+  };
+  int bmax = -1;
+  for (int b = rank; b < nblk; b += cl) bmax = b;
+  // owned row blocks: rows 32b .. 32b+31 (zero beyond n), columns 0 .. 32(b+1)-1
   for (int b = rank; b < nblk; b += cl) {
-    const int k0 = b * CB;
-    float* blk = own + (size_t)L.own_row0(b) * RS;
-    const int tot = (n - k0) * CB;
-    for (int idx = tid; idx < tot; idx += CTH) {
-      const int r = idx >> 5, c = idx & 31;
-      blk[(size_t)r * RS + c] = (k0 + c < n) ? A[(int64_t)(k0 + r) * lda + k0 + c] : 0.f;
+    float* X = blk(b);
+    const int ld = Layout::ldb(b), w = CB * (b + 1);
+    for (int idx = tid; idx < CB * w; idx += CTH) {
+      const int r = idx / w, c = idx - r * w, g = b * CB + r;
+      X[(size_t)r * ld + c] = (g < n && c < n) ? A[(int64_t)g * lda + c] : 0.f;
     }
   }
   __syncthreads();
-  // prof (optional, NULL in the library): globaltimer stamps, 8 per CTA and
-  // block column: wait done, panel copied, look-ahead update, diagonal factor,
-  // inverse, panel, end of the step
-  unsigned long long* pf = prof ? prof + (size_t)rank * nblk * 8 : nullptr;
-  if (rank == 0) factor_block(L, own, li_all, scr, 0, diag0, rel_tol, &bad, pf ? pf + 3 : nullptr);
+  if (rank == 0 && warp == 0) {  // diagonal block 0
+    if (factor_diag(blk(0), Layout::ldb(0), nbr(0), diag0, rel_tol, scr) && tid == 0) bad = 1;
+    invert_diag(scr, lib(0));
+  }
   __syncthreads();
   cluster_arrive();
   for (int k = 0; k < nblk; ++k) {
-    cluster_wait();  // block column k is factored and visible cluster-wide
+    cluster_wait();  // diagonal block k and the panel rows of block column k-1 are ready
     if (pf && tid == 0) pf[8 * k] = gtime();
-    const int ok = k % cl;
-    int jn = rank;  // first owned block column after k
-    while (jn <= k) jn += cl;
-    const float* P;
-    int prow0;
-    if (ok == rank) {
-      P = own + (size_t)L.own_row0(k) * RS;
-      prow0 = k * CB;
-    } else {
-      prow0 = (k + 1) * CB;
-      P = pbuf;
-      if (jn < nblk) {
-        // copy panel rows jn*32 .. n-1 of block column k out of its owner
-        const Layout Lo{n, nblk, cl, ok};
-        const unsigned src = map_rank(own, ok) +
-                             (unsigned)(((size_t)Lo.own_row0(k) + (size_t)(jn - k) * CB) * RS *
-                                        sizeof(float));
-        float* dst = pbuf + (size_t)(jn - k - 1) * CB * RS;
-        const int tot = (n - jn * CB) * (CB / 4);
-        for (int base = tid; base < tot; base += 4 * CTH) {
-          float4 v[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * CTH;
-            if (idx < tot)
-              v[u] = ld_cluster4(src + (unsigned)(((idx >> 3) * RS + (idx & 7) * 4) * sizeof(float)));
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * CTH;
-            if (idx < tot) *reinterpret_cast<float4*>(dst + (idx >> 3) * RS + (idx & 7) * 4) = v[u];
-          }
-        }
+    const int ok = L.owner(k);
+    const bool below = bmax > k;  // owns a row block below k
+    const bool next_owner = k + 1 < nblk && L.owner(k + 1) == rank;
+    const int jb = first_after(k);
+    const int gbase = k * CB;
+    const int gend = below ? min(n, CB * (bmax + 1)) : gbase;
+    // (a) inverse of diagonal block k
+    const float* linv = (ok == rank) ? lib(k) : lcur;
+    if (ok != rank && below) {
+      const Layout Lo{n, nblk, cl, ok};
+      const size_t off = (size_t)Lo.li_off() + (size_t)((k - ok) / cl) * CB * RS;
+      for (int idx = tid; idx < CB * CB / 4; idx += CTH) {
+        const int r = idx >> 3, q4 = (idx & 7) * 4;
+        *reinterpret_cast<float4*>(lcur + r * RS + q4) =
+            ld_cluster4(map_rank(cc_smem + off + r * RS + q4, ok));
       }
     }
+    // (b) panel rows of block column k-1 for row blocks k and k+1
+    if (k >= 1 && below) gather_rows(L, cc_smem, gbuf, gbase, k - 1, gbase, min(gend, gbase + 2 * CB));
     __syncthreads();
     if (pf && tid == 0) pf[8 * k + 1] = gtime();
-    if (k + 1 < nblk && (k + 1) % cl == rank) {  // look-ahead: next block column first
-      update_block(own + (size_t)L.own_row0(k + 1) * RS, (k + 1) * CB, n, P, prow0);
+    // (c) panel k-1 on block column k of the owned row blocks below k, and on
+    //     diagonal block k+1 if owned
+    if (k >= 1) {
+      int ntile = 0;
+      for (int b = jb; b < nblk; b += cl) ++ntile;
+      const int ntask = 4 * (ntile + (next_owner ? 1 : 0));
+      for (int t = warp; t < ntask; t += nwarp) {
+        const int tile = t >> 2, qr = t & 3;
+        const int b = tile < ntile ? jb + tile * cl : k + 1;
+        const int j = tile < ntile ? k : k + 1;
+        float* X = blk(b);
+        const int ld = Layout::ldb(b);
+        tile_rows(X + j * CB, ld, X + (k - 1) * CB, ld, gbuf + (size_t)(j * CB - gbase) * RS, RS,
+                  min(CB, n - j * CB), qr * 8, qr * 8 + 8);
+      }
       __syncthreads();
-      if (pf && tid == 0) pf[8 * k + 2] = gtime();
-      factor_block(L, own, li_all, scr, k + 1, diag0, rel_tol, &bad,
-                   pf ? pf + 8 * (k + 1) + 3 : nullptr);
+    }
+    if (pf && tid == 0) pf[8 * k + 2] = gtime();
+    // (d) panel rows of block column k for the owned row blocks below k
+    {
+      int ntile = 0;
+      for (int b = jb; b < nblk; b += cl) ++ntile;
+      for (int t = warp; t < 4 * ntile; t += nwarp) {
+        const int b = jb + (t >> 2) * cl, qr = t & 3;
+        panel_tile_rows(blk(b) + k * CB, Layout::ldb(b), linv, qr * 8, qr * 8 + 8);
+      }
+      __syncthreads();
+    }
+    if (pf && tid == 0) pf[8 * k + 3] = gtime();
+    // (e) look-ahead: panel k on diagonal block k+1, then factor and invert it
+    if (next_owner) {
+      float* X = blk(k + 1);
+      const int ld = Layout::ldb(k + 1);
+      if (warp < 4) tile_rows(X + (k + 1) * CB, ld, X + k * CB, ld, X + k * CB, ld, nbr(k + 1),
+                              warp * 8, warp * 8 + 8);
+      __syncthreads();
+      if (pf && tid == 0) pf[8 * k + 4] = gtime();
+      if (warp == 0) {
+        if (factor_diag(X + (k + 1) * CB, ld, nbr(k + 1), diag0 + (k + 1) * CB, rel_tol, scr) &&
+            tid == 0)
+          bad = 1;
+        if (pf && tid == 0) pf[8 * k + 7] = gtime();
+        invert_diag(scr, lib(k + 1));
+      }
+      __syncthreads();
+      if (pf && tid == 0) pf[8 * k + 5] = gtime();
     }
     if (k + 1 < nblk) cluster_arrive();
-    for (int j = jn; j < nblk; j += cl)
-      if (j != k + 1) update_block(own + (size_t)L.own_row0(j) * RS, j * CB, n, P, prow0);
+    // (f) remaining rows of block column k-1, then panel k-1 on blocks (b, j),
+    //     b > k+1 owned, k+1 <= j <= b
+    if (k >= 1 && below) {
+      if (gend > gbase + 2 * CB) {
+        gather_rows(L, cc_smem, gbuf, gbase, k - 1, gbase + 2 * CB, gend);
+        __syncthreads();
+      }
+      const int b0 = first_after(k + 1);
+      int ntile = 0;
+      for (int b = b0; b < nblk; b += cl) ntile += b - k;
+      for (int t = warp; t < 4 * ntile; t += nwarp) {
+        int tile = t >> 2, b = b0;
+        while (tile >= b - k) {
+          tile -= b - k;
+          b += cl;
+        }
+        const int j = k + 1 + tile, qr = t & 3;
+        float* X = blk(b);
+        const int ld = Layout::ldb(b);
+        tile_rows(X + j * CB, ld, X + (k - 1) * CB, ld, gbuf + (size_t)(j * CB - gbase) * RS, RS,
+                  min(CB, n - j * CB), qr * 8, qr * 8 + 8);
+      }
+    }
     __syncthreads();
     if (pf && tid == 0) pf[8 * k + 6] = gtime();
   }
 
-  // 64 x 64 inverses: each owner writes its 32 x 32 inverses into their
-  // quadrants; the owner of an even block column adds the lower-left one.
-  const int warp = tid >> 5;
+  // 64 x 64 inverses of the diagonal blocks of L
   for (int b = rank; b < nblk; b += cl) {
-    const float* li = li_all + (size_t)((b - rank) / cl) * CB * RS;
     float* out = dinv + (size_t)(b >> 1) * CHOL_NB * CHOL_NB;
     const int qo = (b & 1) * CB;
-    // own inverse into its quadrant; zero the upper-right quadrant
+    const float* li = lib(b);
     for (int idx = tid; idx < CB * CB; idx += CTH) {
       const int r = idx >> 5, c = idx & 31;
       out[(qo + r) * CHOL_NB + qo + c] = li[r * RS + c];
-      if (qo == 0) out[r * CHOL_NB + CB + c] = 0.f;
+      if (qo == 0) {
+        out[r * CHOL_NB + CB + c] = 0.f;
+        if (b + 1 == nblk) {  // no partner: C^{-1} = I, lower-left zero
+          out[(CB + r) * CHOL_NB + CB + c] = (r == c) ? 1.f : 0.f;
+          out[(CB + r) * CHOL_NB + c] = 0.f;
+        }
+      }
     }
-    if ((b & 1) || warp != 0) continue;
-    combine_64(L, own, li_all, scr, b, out);
+    if ((b & 1) && warp == 0) combine_64(L, cc_smem, blk(b), Layout::ldb(b), li, scr, b, out);
   }
-  // factor back to global memory: lower triangle of the owned block columns
+  // factor back to global memory: lower triangle of the owned row blocks
   for (int b = rank; b < nblk; b += cl) {
-    const int k0 = b * CB;
-    const float* blk = own + (size_t)L.own_row0(b) * RS;
-    const int tot = (n - k0) * CB;
-    for (int idx = tid; idx < tot; idx += CTH) {
-      const int r = idx >> 5, c = idx & 31;
-      if (k0 + c < n && (r >= CB || c <= r)) A[(int64_t)(k0 + r) * lda + k0 + c] = blk[(size_t)r * RS + c];
+    const float* X = blk(b);
+    const int ld = Layout::ldb(b), w = min(n, CB * (b + 1));
+    for (int idx = tid; idx < CB * w; idx += CTH) {
+      const int r = idx / w, c = idx - r * w, g = b * CB + r;
+      if (g < n && c <= g) A[(int64_t)g * lda + c] = X[(size_t)r * ld + c];
     }
   }
   if (tid == 0 && bad) set_status(st, VL_ERR_RANK);
-  // no CTA may leave while a partner may still read its shared memory
+  // no CTA may leave while a peer may still read its shared memory
   cluster_arrive();
   cluster_wait();
 }
@@ -491,15 +554,18 @@ bool launch_chol_cluster(float* A, int64_t lda, int n, float* dinv, const double
   if (n < 1 || n > CL_NMAX) return false;
   const int nblk = (n + CB - 1) / CB;
   const int cl = std::min(CL_MAX, nblk);
-  const size_t smem = cluster_chol_smem(n, cl, 0);  // rank 0 owns the most rows
-  static int attr_smem = 0;
-  if ((int)smem > attr_smem) {
+  size_t smem = 0;
+  for (int r = 0; r < cl; ++r) smem = std::max(smem, cluster_chol_smem(n, cl, r));
+  static size_t attr_smem = 0;
+  if (smem > attr_smem) {
+    size_t need = 0;
+    for (int r = 0; r < CL_MAX; ++r) need = std::max(need, cluster_chol_smem(CL_NMAX, CL_MAX, r));
     if (cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cluster_chol_smem(CL_NMAX, CL_MAX, 0)) != cudaSuccess) {
+                             (int)need) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    attr_smem = (int)cluster_chol_smem(CL_NMAX, CL_MAX, 0);
+    attr_smem = need;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl, 1, 1);
