@@ -41,8 +41,8 @@ SFU_PER_SM_CLK = 32  # ex2 results per SM per clock on this part
 # DRAM bytes per launch of the pairwise kernel at m=400, n=2500 from one ncu
 # capture (profiles/pairwise_f32_finance_m400.md), valid only for the kernel
 # source it was taken on: reported as null once the source changes.
-PAIRWISE_TRAFFIC = {"sha1": "2d8028fff11da1afa4d78092fbae136d09ec5bd8",
-                    "bytes": 5389824 + 479488, "m": 400, "n": 2500}
+PAIRWISE_TRAFFIC = {"sha1": "4d3ec53c751b6a66e6b28ff9c9d64373bbd78297",
+                    "bytes": 4911360 + 1792, "m": 400, "n": 2500}
 MAX_SM_MHZ = 2070.0
 
 
