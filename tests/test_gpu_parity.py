@@ -199,6 +199,35 @@ def test_fused_call_matches_steps(vl, h, prec):
     assert (a["Btau"] - b["Btau"]).abs().max().item() <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_fused_call_replays_from_a_cuda_graph(vl, prec):
+    """After one call of a shape, vl_fit launches nothing that stream capture
+    rejects (no allocation, no synchronisation): captured once into a CUDA graph
+    and replayed on new data of the same shape it gives the eager results."""
+    a = synth.make_config("fmri")
+    rng = np.random.default_rng(5)
+    Xb = a.X + 0.1 * rng.standard_normal(a.X.shape)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = vl.Handle(stream=stream)
+        X = torch.from_numpy(a.X).cuda()
+        out = vl.alloc_outputs(a.m, a.p)
+        vl.vl_fit(h, X, a.p, prec, out["M"], out["order"], out["B0"], out["Btau"], out["D"])
+        h.sync()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            vl.vl_fit(h, X, a.p, prec, out["M"], out["order"], out["B0"], out["Btau"], out["D"])
+        for Xn in (a.X, Xb):
+            X.copy_(torch.from_numpy(Xn))
+            g.replay()
+            stream.synchronize()
+            ref = vl.fit(h, torch.from_numpy(Xn).cuda(), a.p, prec=prec)
+            assert torch.equal(out["order"], ref["order"])
+            for k in ("M", "D", "B0", "Btau"):
+                assert torch.equal(out[k], ref[k]), k
+        h.close()
+
+
 def test_batched_mixed_sizes_match_single_calls(vl, h):
     """A batch of series of different (m, n, p), one of them ill-posed: every
     valid instance equals its single fused call; the bad one reports its own
