@@ -23,6 +23,10 @@ Contents (all in :mod:`oracle.fp64`):
 * ``btau``               B_tau = (I - B0) M_tau.
 * ``varlingam``          the whole pipeline, heuristic or standard.
 
+:mod:`oracle.parallel` runs the same functions with the rows of E_r on a
+process pool, only to time the oracle on all host cores (its results are the
+serial oracle's, bit for bit; a test checks that).
+
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, quadrature, brute force or library routines, except the
 literature constant k1 = 79.047 of ``entropy`` (reproduced to 4 digits by a

@@ -6,6 +6,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch
 import torch.distributed as dist
@@ -66,3 +67,22 @@ def test_max_over_ranks_two_gloo_ranks():
         assert p.exitcode == 0
     res = dict(q.get(timeout=10) for _ in range(2))
     assert res == {0: 15.0, 1: 15.0}
+
+
+def test_oracle_process_pool_driver_equals_the_oracle():
+    """The all-cores CPU baseline runs the oracle's own functions on a process
+    pool; its results must be the oracle's, bit for bit."""
+    import multiprocessing as mp
+
+    import oracle
+    import oracle.parallel as op
+    import synth
+
+    inst = synth.make_config("pr1")
+    with mp.get_context("spawn").Pool(2) as pool:
+        a = op.varlingam_pool(inst.X, inst.p, pool, 2)
+    b = oracle.varlingam(inst.X, inst.p)
+    assert np.array_equal(a["D"], b["D"])
+    assert list(a["order"]) == list(b["order"])
+    assert np.array_equal(a["B0"], b["B0"])
+    assert np.array_equal(a["Btau"], b["Btau"])
