@@ -917,6 +917,7 @@ template void chol_blocked<double>(const Ctx&, double*, int64_t, int, double*, d
 template <class T>
 void chol_solve_blocked(const Ctx& cx, const T* L, int64_t lda, const T* dinv, int n, T* R,
                         int64_t ldr, int nrhs, bool backward) {
+  if (launch_trsm_ring<T>(L, lda, dinv, n, R, ldr, nrhs, backward, cx.s)) return;
   const size_t smem = trsm_smem_bytes<T>();
   static bool attr_set = false;
   if (!attr_set) {

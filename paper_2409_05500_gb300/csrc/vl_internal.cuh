@@ -153,6 +153,11 @@ size_t gemm_part_need(int M, int N, int K);
 // dinv (T, ceil(n/nb) blocks of nb*nb).  diag0 (n doubles) receives the
 // original diagonal; a pivot below 1e-6 (FP32) / 1e-12 (FP64) of it sets
 // VL_ERR_RANK.
+// Triangular solves with the solution panel in shared memory (n <= 1024);
+// false if not launched (the caller then uses trsm_cols_kernel).
+template <class T>
+bool launch_trsm_ring(const T* L, int64_t lda, const T* dinv, int n, T* R, int64_t ldr, int nrhs,
+                      bool backward, cudaStream_t s);
 // Cholesky of an FP32 matrix with n <= 512 on one thread-block cluster; false
 // if not launched (n out of range or no cluster resources).
 bool launch_chol_cluster(float* A, int64_t lda, int n, float* dinv, const double* diag0,
