@@ -198,13 +198,21 @@ def relative_gap(scores: Dict[int, float]) -> float:
     return (s2 - s1) / max(abs(s1), abs(s2), 1e-300)
 
 
-def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1e-6
-                 ) -> Tuple[bool, int, List[int]]:
+def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1e-6,
+                 D_cand: Optional[np.ndarray] = None) -> Tuple[bool, int, List[int]]:
     """Order comparison rule: walk the candidate order step by step over ITS
     OWN remaining set U; at each step the pick must be a minimiser of the
     reference scores (Eq. 3 over D_ref), unless the reference scores of the
     pick and the true minimiser lie within `rel_gap` relative of each other
     (a near tie, where either choice is correct up to rounding).
+
+    With D_cand (the matrix the candidate ordered, equal to D_ref up to the
+    measure's tolerance), a step also passes when the two reference scores are
+    closer than the change of those scores that the difference D_cand - D_ref
+    itself produces: sum over U of |min(0, D_cand)^2 - min(0, D_ref)^2| for the
+    pick plus the same for the minimiser.  The order is then Algorithm 1's on
+    the candidate's own D, and the difference comes from D, which is checked
+    against its own tolerance.
 
     Returns (ok, number of near-tie steps, list of failing steps)."""
     D_ref = np.asarray(D_ref, dtype=np.float64)
@@ -214,14 +222,24 @@ def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1
     bad: List[int] = []
     if sorted(int(c) for c in order_gpu) != list(range(m)):
         return False, 0, [-1]
+    dP = None
+    if D_cand is not None:
+        D_cand = np.asarray(D_cand, dtype=np.float64)
+        dP = np.abs(np.minimum(0.0, D_cand) ** 2 - np.minimum(0.0, D_ref) ** 2)
+        np.fill_diagonal(dP, 0.0)
     for k, c in enumerate(order_gpu):
         c = int(c)
         scores = scores_over(D_ref, U)
-        smin = min(scores.values())
+        imin = min(scores, key=lambda i: (scores[i], i))
+        smin = scores[imin]
         sc = scores[c]
         if sc != smin:
             denom = max(abs(sc), abs(smin), 1e-300)
-            if (sc - smin) / denom <= rel_gap:
+            band = 0.0
+            if dP is not None:
+                Ua = np.asarray(U)
+                band = dP[c, Ua].sum() + dP[imin, Ua].sum()
+            if (sc - smin) / denom <= rel_gap or sc - smin <= band:
                 ties += 1
             else:
                 bad.append(k)

@@ -101,6 +101,30 @@ def test_gap_rule_accepts_ties_and_rejects_swaps():
     assert oracle.order_gap_ok([2, 0, 1], Z) == (True, 0, [])  # every pick is a minimiser
 
 
+def test_gap_rule_band_from_the_candidates_own_measure():
+    """A difference of order that the candidate's D explains (its own
+    Algorithm 1 order, D within a small perturbation of the reference) passes
+    with D_cand; the same order without D_cand, or a swap that D_cand does not
+    explain, fails."""
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        A = rng.normal(size=(7, 7))
+        D = A - A.T
+        ref = [int(c) for c in oracle.order_heuristic(D)["order"]]
+        E = rng.normal(size=(7, 7)) * 0.05
+        Dc = D + (E - E.T)
+        cand = [int(c) for c in oracle.order_heuristic(Dc)["order"]]
+        if cand != ref and not oracle.order_gap_ok(cand, D)[0]:
+            break
+    else:
+        raise AssertionError("no perturbation changed the order")
+    assert oracle.order_gap_ok(cand, D, D_cand=Dc)[0]
+    assert not oracle.order_gap_ok(cand, D)[0]
+    worse = ref[::-1]  # not explained by a 5 % perturbation
+    assert not oracle.order_gap_ok(worse, D, D_cand=Dc)[0]
+    assert oracle.order_gap_ok(ref, D, D_cand=Dc)[0]
+
+
 def test_incremental_scores_equal_recomputed():
     """The running-sum form S_i -= P_{i,c} (what a GPU does) selects the same
     order as the literal recompute of Algorithm 1."""
