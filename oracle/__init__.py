@@ -19,6 +19,8 @@ Contents (all in :mod:`oracle.fp64`):
                          precomputed tables.
 * ``order_standard``     the iterative DirectLiNGAM search with the data
                          refinement of Eq. 4 (Section 3, steps 1-5).
+* ``order_gap_ok`` / ``order_standard_gap_ok``  the order comparison rules
+                         (near ties of Eq. 3 may go either way).
 * ``b0_ols`` / ``b0_ldl`` two independent routes to B0 from a causal order.
 * ``btau``               B_tau = (I - B0) M_tau.
 * ``varlingam``          the whole pipeline, heuristic or standard.
@@ -47,6 +49,7 @@ from .fp64 import (  # noqa: F401
     order_gap_ok,
     order_heuristic,
     order_standard,
+    order_standard_gap_ok,
     pairwise_measure,
     relative_gap,
     residual,

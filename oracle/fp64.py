@@ -247,6 +247,55 @@ def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1
     return (not bad), ties, bad
 
 
+def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: float = 1e-6,
+                          d_tol: float = 0.0) -> Tuple[bool, int, List[int]]:
+    """Order comparison rule for the iterative search of Section 3: the
+    search of :func:`order_standard` is replayed, but every iteration removes
+    the CANDIDATE's pick and refines the remaining variables on it (Eq. 4), so
+    that one early near tie does not make every later step incomparable.  At
+    each iteration the pick must minimise the reference scores (Eq. 3 over the
+    D of that iteration's data), unless the two scores lie within `rel_gap`
+    relative of each other, or within the band that a difference of at most
+    d_tol * max|D| in every entry of D can produce: for one score that is the
+    sum over U of 2 |D_ij| delta + delta^2, taken for the pick and for the
+    minimiser.
+
+    Returns (ok, number of near-tie steps, list of failing steps)."""
+    X = np.array(Xs, dtype=np.float64, copy=True)
+    m = X.shape[0]
+    if sorted(int(c) for c in order_cand) != list(range(m)):
+        return False, 0, [-1]
+    U = list(range(m))
+    ties = 0
+    bad: List[int] = []
+    for k, c in enumerate(order_cand):
+        c = int(c)
+        if len(U) == 1:
+            break
+        D = pairwise_measure(standardize(X[U]))["D"]
+        loc = {v: a for a, v in enumerate(U)}
+        sub = scores_over(D, range(len(U)))
+        scores = {v: sub[loc[v]] for v in U}
+        imin = min(U, key=lambda i: (scores[i], i))
+        sc, smin = scores[c], scores[imin]
+        if sc != smin:
+            denom = max(abs(sc), abs(smin), 1e-300)
+            delta = d_tol * np.abs(D).max()
+            A = np.abs(D)
+            np.fill_diagonal(A, 0.0)
+            nb = len(U) - 1
+            band = (2.0 * delta * (A[loc[c]].sum() + A[loc[imin]].sum())
+                    + 2.0 * nb * delta * delta)
+            if (sc - smin) / denom <= rel_gap or sc - smin <= band:
+                ties += 1
+            else:
+                bad.append(k)
+        U.remove(c)
+        for j in U:  # Eq. 4 on the candidate's pick
+            X[j] = residual(X[j], X[c])
+    return (not bad), ties, bad
+
+
 # --------------------------------------------------------- B0 and B_tau
 def b0_ols(E: np.ndarray, order: Sequence[int]) -> np.ndarray:
     """B0 from a causal order (Section 4: the instantaneous matrix of

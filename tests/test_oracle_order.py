@@ -141,3 +141,50 @@ def test_incremental_scores_equal_recomputed():
         U.remove(c)
         S = S - P[:, c]
     assert order == [int(c) for c in oracle.order_heuristic(D)["order"]]
+
+
+def test_standard_walk_accepts_its_own_order_and_rejects_swaps():
+    """The comparison rule of the iterative search replays order_standard
+    exactly when given its own order (every pick is the minimiser: no ties),
+    rejects a swap at a well-separated step, and accepts that swap only when
+    the allowed D difference is large enough to explain it."""
+    inst = synth.make_instance(7, 4000, 1, 77, "uniform", 0.4, 0.3, 0.8, "unif", 0.3)
+    M, E = oracle.var_ols(inst.X, 1)
+    Xs = oracle.standardize(E)
+    od = oracle.order_standard(Xs)
+    own = [int(c) for c in od["order"]]
+    assert oracle.order_standard_gap_ok(Xs, own) == (True, 0, [])
+    # the first step with a clear gap: swap its pick with the runner-up
+    k = next(k for k, st in enumerate(od["steps"][:-1])
+             if oracle.relative_gap(st["scores"]) > 1e-2)
+    sc = od["steps"][k]["scores"]
+    runner = sorted(sc, key=lambda i: (sc[i], i))[1]
+    cand = own[:k] + [runner] + [c for c in own[k:] if c != runner]
+    ok, ties, bad = oracle.order_standard_gap_ok(Xs, cand)
+    assert not ok and bad[0] == k
+    assert oracle.order_standard_gap_ok(Xs, cand, d_tol=1.0)[0]
+    assert not oracle.order_standard_gap_ok(Xs, own[:-1] + [own[0]])[0]
+
+
+def test_standard_walk_follows_the_candidates_refinement():
+    """A candidate that takes a non-minimiser early (allowed here as a tie by
+    a loose rel_gap) is compared afterwards on the data refined on ITS pick:
+    its later steps, taken as order_standard would on that data, pass with no
+    further ties; comparing them on the reference's refinement would not
+    be the same computation."""
+    inst = synth.make_instance(6, 3000, 1, 311, "laplace", 0.4, 0.3, 0.8, "unif", 0.3)
+    M, E = oracle.var_ols(inst.X, 1)
+    Xs = oracle.standardize(E)
+    od = oracle.order_standard(Xs)
+    sc = od["steps"][0]["scores"]
+    first = sorted(sc, key=lambda i: (sc[i], i))[1]   # the runner-up as first pick
+    X = Xs.copy()
+    rest = [j for j in range(6) if j != first]
+    for j in rest:
+        X[j] = oracle.residual(X[j], X[first])
+    tail = oracle.order_standard(X[rest])["order"]
+    cand = [first] + [rest[int(a)] for a in tail]
+    ok, ties, bad = oracle.order_standard_gap_ok(Xs, cand, rel_gap=10.0)
+    assert ok and ties == 1
+    ok0, _, bad0 = oracle.order_standard_gap_ok(Xs, cand)
+    assert not ok0 and bad0 == [0]
