@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-standard", action="store_true",
+                    help="skip timing the iterative search of Section 3")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batched", action="store_true",
                     help="also time the 256-series mixed-size batch (vl_fit_batched)")
@@ -317,6 +319,32 @@ def run_ours(args, rank, world):
     phases = {nm: round(marks[i].elapsed_time(marks[i + 1]), 4) for i, nm in
               enumerate(["var_fit", "pairwise_measure", "causal_order", "fit_b"])}
 
+    # the iterative search of Section 3 on the same residuals (the method
+    # Algorithm 1 approximates), against Algorithm 1's measure + order phases
+    standard = None
+    if not args.no_standard and args.prec == "mixed":
+        so = torch.empty(m, dtype=torch.int32, device=f"cuda:{dev}")
+        vl.vl_causal_order_standard(h, E, "mixed", so)
+        h.sync()
+        sms_std, host_std = [], []
+        l0 = vl.kernel_launches()
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t0 = time.perf_counter()
+            vl.vl_causal_order_standard(h, E, "mixed", so)
+            host_std.append((time.perf_counter() - t0) * 1e3)
+            b.record(stream)
+            h.sync()
+            sms_std.append(a.elapsed_time(b))
+        heur = phases["pairwise_measure"] + phases["causal_order"]
+        std_ms = statistics.median(sms_std)
+        standard = {"ms": round(std_ms, 3), "host_enqueue_ms": round(statistics.median(host_std), 3),
+                    "launches": (vl.kernel_launches() - l0) // 3,
+                    "algorithm1_ms": round(heur, 4), "ratio_to_algorithm1": round(std_ms / heur, 1),
+                    "same_first_pick": bool(so[0].item() == out["order"][0].item())}
+
     # FP64 GPU comparison path (same steps, every kernel in FP64)
     fp64_ms = None
     if not args.no_fp64_compare and args.prec == "mixed":
@@ -386,6 +414,7 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single"},
         "fp64_ms_per_step": fp64_ms,
         "phase_ms": phases,
+        "standard_search": standard,
         "e2e": {"value": job_throughput(PS, world, e2e_step), "unit": UNIT, "ms_per_step": e2e_step,
                 "h2d_bytes_per_step": Xh.numel() * Xh.element_size(),
                 "d2h_bytes_per_step": d2h},

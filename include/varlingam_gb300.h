@@ -159,6 +159,34 @@ vl_status vl_causal_order_noalloc(void* cuda_stream, const double* D, int m, int
                                   double* gap);
 
 /*
+ * The iterative DirectLiNGAM search (Sec. 3, steps 1-5), the method that
+ * Algorithm 1 approximates: with U = all variables, repeat until one is left
+ *   1. standardize every x_i, i in U (population variance);
+ *   2-3. the pairwise measure D over U, as vl_pairwise_measure computes it
+ *        (Eqs. 1-2), on the CURRENT data;
+ *   4. pick c = argmin_{i in U} sum_{j in U, j != i} min(0, D_ij)^2 (Eq. 3;
+ *      ties -> lowest index), append it to the order, remove it from U;
+ *   5. replace every x_j, j in U, by its residual on the pick,
+ *      x_j - cov(x_j, x_c) / var(x_c) x_c (Eq. 4).
+ * The last variable closes the order.  Cost: sum over u = m..2 of the
+ * measure of u variables, about m/3 times the pairwise work of Algorithm 1.
+ * E     : m x n_eff data (the VAR residuals), row stride lde >= n_eff; read only.
+ * prec  : the precision of each pairwise measure (as vl_pairwise_measure);
+ *         the refinement of step 5 is FP64 in both modes.
+ * order : output m int32 (causes first).
+ * gap   : output m doubles or NULL; gap[k] = relative gap between the two
+ *         smallest scores of iteration k, as in vl_causal_order (+inf last).
+ * Runs asynchronously on the handle's stream with no host synchronisation
+ * (the picks stay on the device); its buffers are the handle's series
+ * buffers (shared with vl_fit, 2 m n_eff + m^2 + 3 m doubles) and workspace,
+ * so after a first call of the same or larger size it allocates nothing.
+ * Device errors (degenerate or non-finite data at any iteration) surface at
+ * vl_sync().  Requires 2 <= m <= VL_MAX_M, n_eff >= 2.
+ */
+vl_status vl_causal_order_standard(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
+                                   vl_precision prec, int32_t* order, double* gap);
+
+/*
  * B0 and B_tau from a causal order (Sec. 4: the instantaneous matrix of
  * VarLiNGAM): row order[k] of B0 holds the least-squares coefficients of
  * e_{order[k]} on e_{order[0..k-1]}; then B_tau = (I - B0) M_tau.

@@ -69,6 +69,7 @@ def _load() -> ctypes.CDLL:
         "vl_pairwise_measure": [P, P, I64, I, I, I, P, P, P],
         "vl_causal_order": [P, P, I, P, P],
         "vl_causal_order_noalloc": [P, P, I, P, P],
+        "vl_causal_order_standard": [P, P, I64, I, I, I, P, P],
         "vl_fit_b": [P, P, I64, I, I, P, P, I, I, P, P],
         "vl_fit_batched": [P, ctypes.POINTER(vl_instance), I, I, ctypes.POINTER(I)],
         "vl_fit": [P, P, I64, I, I, I, I, P, P, P, P, P],
@@ -184,6 +185,15 @@ def vl_causal_order_noalloc(D: torch.Tensor, order: torch.Tensor,
                                         _ptr(order), _ptr(gap))
     if code != VL_OK:
         raise VLError(code, "vl_causal_order_noalloc")
+
+
+def vl_causal_order_standard(h: Handle, E: torch.Tensor, prec: str, order: torch.Tensor,
+                             gap: Optional[torch.Tensor] = None) -> None:
+    """The iterative search of Section 3 (Eq. 4 refinement every iteration)."""
+    m, n_eff = E.shape
+    h.check(_lib.vl_causal_order_standard(h.h, _ptr(E), E.stride(0), m, n_eff,
+                                          PRECISIONS[prec], _ptr(order), _ptr(gap)),
+            "vl_causal_order_standard")
 
 
 def vl_fit_b(h: Handle, E: torch.Tensor, order: torch.Tensor, M: Optional[torch.Tensor],

@@ -334,6 +334,64 @@ vl_status order_impl(Exec& x, const double* D, int m, int32_t* order, double* ga
   return check_launch(x.h, "vl_causal_order");
 }
 
+// The iterative search of Sec. 3: m - 1 iterations of (pairwise measure of
+// the u remaining variables, Eq. 3 score + pick, Eq. 4 refinement with
+// compaction), all queued on the stream; the pick stays on the device.
+template <class T>
+vl_status order_standard_impl(Exec& x, const double* E, int64_t lde, int m, int n,
+                              int32_t* order, double* gap) {
+  vl_handle h = x.h;
+  // workspace of the largest measure (every later one is smaller in all
+  // terms except the split count, so take the maximum over all of them)
+  Exec probe{h, nullptr, nullptr, nullptr, nullptr, true, 0};
+  for (int u = m; u >= 2; --u)
+    pairwise_impl<T>(probe, E, lde, u, n, nullptr, nullptr, nullptr, nullptr);
+  vl_status s = grow(h, x.ws, x.ws_cap, probe.need, x.s);
+  if (s != VL_OK) return s;
+  const int64_t ldw = round_up(n, 4);
+  double *W0, *W1, *D, *S;
+  int32_t *idx0, *idx1;
+  int* pick;
+  unsigned* counter;
+  auto carve = [&](Arena& a) {
+    W0 = a.take<double>((size_t)m * ldw);
+    W1 = a.take<double>((size_t)m * ldw);
+    D = a.take<double>((size_t)m * m);
+    S = a.take<double>(m);
+    idx0 = a.take<int32_t>(m);
+    idx1 = a.take<int32_t>(m);
+    pick = a.take<int>(1);
+    counter = a.take<unsigned>(1);
+  };
+  Arena sz;
+  carve(sz);
+  s = grow(h, &h->sbuf, &h->sbuf_cap, sz.off + 512, x.s);
+  if (s != VL_OK) return s;
+  Arena a;
+  a.base = static_cast<char*>(h->sbuf);
+  a.cap = h->sbuf_cap;
+  carve(a);
+  cudaMemsetAsync(counter, 0, sizeof(unsigned), x.s);
+  const double* src = E;
+  int64_t lds = lde;
+  const int32_t* isrc = nullptr;  // identity at the first iteration
+  double* Wdst = W0;
+  int32_t* idst = idx0;
+  for (int k = 0; k + 1 < m; ++k) {
+    const int u = m - k;
+    s = pairwise_impl<T>(x, src, lds, u, n, nullptr, nullptr, D, nullptr);
+    if (s != VL_OK) return s;
+    launch_std_score_pick(D, u, S, counter, isrc, order, gap, k, pick, x.st, x.s);
+    launch_std_refine(src, lds, u, n, pick, isrc, Wdst, ldw, idst, order, gap, k, x.s);
+    src = Wdst;
+    lds = ldw;
+    isrc = idst;
+    Wdst = Wdst == W0 ? W1 : W0;
+    idst = idst == idx0 ? idx1 : idx0;
+  }
+  return check_launch(h, "vl_causal_order_standard");
+}
+
 // The whole method on one series, on one execution context.  E, C and D are
 // per-series buffers of the caller (E: m x (n-p), C, D: m x m).
 template <class T>
@@ -610,6 +668,21 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
   DeviceGuard g(h->device);
   Exec x = handle_exec(h);
   return order_impl(x, D, m, order, gap);
+}
+
+vl_status vl_causal_order_standard(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
+                                   vl_precision prec, int32_t* order, double* gap) {
+  if (!h) return VL_ERR_ARG;
+  if (!E || !order)
+    return fail(h, VL_ERR_ARG, "vl_causal_order_standard: E and order must not be NULL");
+  if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
+  if (m < 2 || n_eff < 2 || m > VL_MAX_M || lde < n_eff)
+    return fail(h, VL_ERR_SHAPE,
+                "vl_causal_order_standard: need 2 <= m <= VL_MAX_M, n_eff >= 2, lde >= n_eff");
+  DeviceGuard g(h->device);
+  Exec x = handle_exec(h);
+  return prec == VL_PREC_MIXED ? order_standard_impl<float>(x, E, lde, m, n_eff, order, gap)
+                               : order_standard_impl<double>(x, E, lde, m, n_eff, order, gap);
 }
 
 vl_status vl_fit_b(vl_handle h, const double* E, int64_t lde, int m, int n_eff,

@@ -45,6 +45,9 @@ def test_null_handle_is_rejected_on_the_host(lib):
     assert lib.vl_var_fit(None, None, 10, 3, 10, 1, 1, None, None) == 1
     lib.vl_sync.argtypes = [P]
     assert lib.vl_sync(None) == 1
+    lib.vl_causal_order_standard.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, P, P]
+    assert lib.vl_causal_order_standard(None, None, 10, 3, 10, 1, None, None) == 1
     lib.vl_last_error.restype = ctypes.c_char_p
     lib.vl_last_error.argtypes = [P]
     assert lib.vl_last_error(None) == b"null handle"

@@ -256,6 +256,96 @@ def test_batched_mixed_sizes_match_single_calls(vl, h):
         assert (ref["D"] - dicts_b[k]["D"]).abs().max().item() <= 1e-12
 
 
+# ------------------------------------- iterative search (Section 3, Eq. 4)
+# D tolerance behind the comparison band of each iteration: the measure's own
+# tolerance in mixed precision; FP64 measures agree far closer than that.
+STD_DTOL = {"mixed": D_REL, "fp64": 1e-8}
+# Absolute tolerance of the reported gaps: a gap is (S_2 - S_1) / max(S_1, S_2),
+# so score errors of relative size e move it by up to about 2e; e ~ 1e-5 for
+# the FP32 measure, far below for FP64.
+STD_GAP_ATOL = {"mixed": 1e-4, "fp64": 1e-8}
+_std_cache = {}
+
+
+def _std_case(case):
+    if case == "m70_ragged":  # several 64-wide tiles at the start, one at the end; n ragged
+        inst = synth.make_instance(70, 303, 1, 7070, "laplace", 0.1, 0.1, 0.5, "unif", 0.5)
+    else:
+        inst = synth.make_config(case)
+    if case not in _std_cache:
+        M, E = oracle.var_ols(inst.X, inst.p)
+        Xs = oracle.standardize(E)
+        _std_cache[case] = (E, Xs, oracle.order_standard(Xs))
+    return _std_cache[case]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("case", ["pr1", "fmri", "m70_ragged"])
+def test_standard_order_matches_the_iterative_oracle(vl, h, prec, case):
+    """vl_causal_order_standard against the oracle's iterative search on the
+    same VAR residuals, replayed on the GPU's own picks: at every iteration
+    the pick minimises Eq. 3 over that iteration's refined data, unless the
+    two scores lie within 1e-6 relative or within the band a D difference of
+    the measure's tolerance can produce.  Where the oracle's own search has no
+    gap below 1e-3 the two orders are identical."""
+    E, Xs, ref = _std_case(case)
+    m = E.shape[0]
+    Et = torch.from_numpy(np.ascontiguousarray(E)).cuda()
+    order = torch.empty(m, dtype=torch.int32, device="cuda")
+    gap = torch.empty(m, dtype=torch.float64, device="cuda")
+    vl.vl_causal_order_standard(h, Et, prec, order, gap)
+    h.sync()
+    o = [int(c) for c in order.cpu().numpy()]
+    ok, ties, bad = oracle.order_standard_gap_ok(Xs, o, GAP, STD_DTOL[prec])
+    _report(f"standard order {case} {prec}", ties=ties, bad=len(bad))
+    assert ok, (bad, o)
+    g = gap.cpu().numpy()
+    assert math.isinf(g[-1]) and np.all(g[:-1] >= 0)
+    ref_gaps = [oracle.relative_gap(st["scores"]) for st in ref["steps"]]
+    if min(ref_gaps) > 1e-3:
+        assert o == [int(c) for c in ref["order"]]
+        dg = np.abs(g[:-1] - np.array(ref_gaps[:-1])).max()
+        _report(f"standard gaps {case} {prec}", max_abs_gap_diff=dg)
+        assert dg <= STD_GAP_ATOL[prec], dg
+
+
+def test_standard_first_pick_is_algorithm1_first_pick(vl, h):
+    """Iteration 1 of the search scores the same measure as Algorithm 1's
+    first step: the two entry points pick the same first variable."""
+    E, Xs, ref = _std_case("fmri")
+    m = E.shape[0]
+    Et = torch.from_numpy(np.ascontiguousarray(E)).cuda()
+    f64 = dict(dtype=torch.float64, device="cuda")
+    D = torch.empty((m, m), **f64)
+    vl.vl_pairwise_measure(h, Et, "mixed", None, None, D)
+    o1 = torch.empty(m, dtype=torch.int32, device="cuda")
+    o2 = torch.empty(m, dtype=torch.int32, device="cuda")
+    g1 = torch.empty(m, **f64)
+    vl.vl_causal_order(h, D, o1, g1)
+    vl.vl_causal_order_standard(h, Et, "mixed", o2)
+    h.sync()
+    if g1[0].item() > 1e-6:
+        assert o1[0].item() == o2[0].item()
+
+
+def test_standard_order_reports_degeneracy_after_refinement(vl, h):
+    """x_2 = x_0 + x_1: no pair is collinear, but once one variable is
+    removed by Eq. 4 the other two are, and the next measure reports it."""
+    rng = np.random.default_rng(3)
+    E = rng.laplace(size=(3, 500))
+    E[2] = E[0] + E[1]
+    Et = torch.from_numpy(E).cuda()
+    D = torch.empty((3, 3), dtype=torch.float64, device="cuda")
+    vl.vl_pairwise_measure(h, Et, "fp64", None, None, D)
+    h.sync()  # the data itself is fine
+    order = torch.empty(3, dtype=torch.int32, device="cuda")
+    vl.vl_causal_order_standard(h, Et, "fp64", order)
+    with pytest.raises(vl.VLError) as ei:
+        h.sync()
+    assert ei.value.code == 4
+    h.sync()
+
+
 # ------------------------------------------------------------ errors
 def test_errors_reported(vl, h):
     f64 = dict(dtype=torch.float64, device="cuda")
@@ -309,6 +399,12 @@ def test_bad_arguments(vl, h):
     lib = vl.lib()
     assert lib.vl_causal_order(h.h, None, 4, None, None) == 1
     assert lib.vl_pairwise_measure(h.h, None, 10, 4, 10, 1, None, None, None) == 1
+    assert lib.vl_causal_order_standard(h.h, None, 10, 4, 10, 1, None, None) == 1
+    Et = torch.zeros((1, 100), **f64)
+    with pytest.raises(vl.VLError) as ei:
+        vl.vl_causal_order_standard(h, Et, "mixed", torch.empty(1, dtype=torch.int32,
+                                                                device="cuda"))
+    assert ei.value.code == 2
 
 
 # ------------------------------------------------------- batched workload
