@@ -171,14 +171,17 @@ vl_status vl_causal_order_noalloc(void* cuda_stream, const double* D, int m, int
  * The last variable closes the order.  Cost: sum over u = m..2 of the
  * measure of u variables, about m/3 times the pairwise work of Algorithm 1.
  * E     : m x n_eff data (the VAR residuals), row stride lde >= n_eff; read only.
- * prec  : the precision of each pairwise measure (as vl_pairwise_measure);
- *         the refinement of step 5 is FP64 in both modes.
+ * prec  : the precision of each pairwise measure (as vl_pairwise_measure).
+ *         Step 5 is applied in FP64 with the slopes taken from the centred
+ *         cross products the measure computes for its correlations (FP64,
+ *         or in VL_PREC_MIXED split-FP32 products summed in double-float,
+ *         relative error about 1e-8).
  * order : output m int32 (causes first).
  * gap   : output m doubles or NULL; gap[k] = relative gap between the two
  *         smallest scores of iteration k, as in vl_causal_order (+inf last).
  * Runs asynchronously on the handle's stream with no host synchronisation
  * (the picks stay on the device); its buffers are the handle's series
- * buffers (shared with vl_fit, 2 m n_eff + m^2 + 3 m doubles) and workspace,
+ * buffers (shared with vl_fit, 2 m n_eff + 2 m^2 + 3 m doubles) and workspace,
  * so after a first call of the same or larger size it allocates nothing.
  * Device errors (degenerate or non-finite data at any iteration) surface at
  * vl_sync().  Requires 2 <= m <= VL_MAX_M, n_eff >= 2.

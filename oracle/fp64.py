@@ -248,7 +248,8 @@ def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1
 
 
 def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: float = 1e-6,
-                          d_tol: float = 0.0) -> Tuple[bool, int, List[int]]:
+                          d_tol: float = 0.0, gaps_cand: Optional[Sequence[float]] = None
+                          ) -> Tuple[bool, int, List[int]]:
     """Order comparison rule for the iterative search of Section 3: the
     search of :func:`order_standard` is replayed, but every iteration removes
     the CANDIDATE's pick and refines the remaining variables on it (Eq. 4), so
@@ -259,6 +260,12 @@ def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: fl
     d_tol * max|D| in every entry of D can produce: for one score that is the
     sum over U of 2 |D_ij| delta + delta^2, taken for the pick and for the
     minimiser.
+
+    With gaps_cand (the candidate's relative gap per iteration), an iteration
+    also fails when that gap differs from the reference's (S_(2) - S_(1)) /
+    S_(2) by more than a D difference of d_tol * max|D| explains: if no score
+    moves by more than B (the largest band above), neither do the two
+    smallest, and the gap moves by at most 2 B / (S_(2) - B), plus rel_gap.
 
     Returns (ok, number of near-tie steps, list of failing steps)."""
     X = np.array(Xs, dtype=np.float64, copy=True)
@@ -278,18 +285,29 @@ def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: fl
         scores = {v: sub[loc[v]] for v in U}
         imin = min(U, key=lambda i: (scores[i], i))
         sc, smin = scores[c], scores[imin]
+        delta = d_tol * np.abs(D).max()
+        A = np.abs(D)
+        np.fill_diagonal(A, 0.0)
+        nb = len(U) - 1
+        bands = 2.0 * delta * A.sum(axis=1) + nb * delta * delta  # per local index
+        failed = False
         if sc != smin:
             denom = max(abs(sc), abs(smin), 1e-300)
-            delta = d_tol * np.abs(D).max()
-            A = np.abs(D)
-            np.fill_diagonal(A, 0.0)
-            nb = len(U) - 1
-            band = (2.0 * delta * (A[loc[c]].sum() + A[loc[imin]].sum())
-                    + 2.0 * nb * delta * delta)
+            band = bands[loc[c]] + bands[loc[imin]]
             if (sc - smin) / denom <= rel_gap or sc - smin <= band:
                 ties += 1
             else:
-                bad.append(k)
+                failed = True
+        if gaps_cand is not None:
+            vals = sorted(scores.values())
+            s1, s2 = vals[0], vals[1]
+            g_ref = (s2 - s1) / max(abs(s1), abs(s2), 1e-300)
+            B = bands.max()
+            tol = 2.0 * B / max(s2 - B, 1e-300) + rel_gap
+            if not abs(float(gaps_cand[k]) - g_ref) <= tol:
+                failed = True
+        if failed:
+            bad.append(k)
         U.remove(c)
         for j in U:  # Eq. 4 on the candidate's pick
             X[j] = residual(X[j], X[c])

@@ -213,7 +213,10 @@ vl_status pairwise_impl(Exec& x, const double* E, int64_t lde, int m, int n, dou
                         double* Hr, double* D, double* C_out) {
   const bool f32 = sizeof(T) == 4;
   PairPlan pl = plan_pairwise(m, n, x.h->num_sms, !f32);
-  const size_t part_cap = (size_t)16 * m * m;
+  // split-K scratch of the covariance: 16 m^2, at least 64 m^2 up to 8 MB, so
+  // that a small product still splits its long K over enough CTAs
+  const size_t part_cap =
+      std::max((size_t)16 * m * m, std::min((size_t)64 * m * m, (size_t)1 << 20));
   // FP32 path: 4 floats (2 double-float sums) per residual per split;
   // FP64 path: 2 doubles
   const size_t nparts = (size_t)pl.splits * 2 * m * m;  // in 8-byte units
@@ -349,7 +352,7 @@ vl_status order_standard_impl(Exec& x, const double* E, int64_t lde, int m, int 
   vl_status s = grow(h, x.ws, x.ws_cap, probe.need, x.s);
   if (s != VL_OK) return s;
   const int64_t ldw = round_up(n, 4);
-  double *W0, *W1, *D, *S;
+  double *W0, *W1, *D, *C, *S;
   int32_t *idx0, *idx1;
   int* pick;
   unsigned* counter;
@@ -357,6 +360,7 @@ vl_status order_standard_impl(Exec& x, const double* E, int64_t lde, int m, int 
     W0 = a.take<double>((size_t)m * ldw);
     W1 = a.take<double>((size_t)m * ldw);
     D = a.take<double>((size_t)m * m);
+    C = a.take<double>((size_t)m * m);
     S = a.take<double>(m);
     idx0 = a.take<int32_t>(m);
     idx1 = a.take<int32_t>(m);
@@ -379,10 +383,10 @@ vl_status order_standard_impl(Exec& x, const double* E, int64_t lde, int m, int 
   int32_t* idst = idx0;
   for (int k = 0; k + 1 < m; ++k) {
     const int u = m - k;
-    s = pairwise_impl<T>(x, src, lds, u, n, nullptr, nullptr, D, nullptr);
+    s = pairwise_impl<T>(x, src, lds, u, n, nullptr, nullptr, D, C);
     if (s != VL_OK) return s;
     launch_std_score_pick(D, u, S, counter, isrc, order, gap, k, pick, x.st, x.s);
-    launch_std_refine(src, lds, u, n, pick, isrc, Wdst, ldw, idst, order, gap, k, x.s);
+    launch_std_refine(src, lds, u, n, C, pick, isrc, Wdst, ldw, idst, order, gap, k, x.s);
     src = Wdst;
     lds = ldw;
     isrc = idst;

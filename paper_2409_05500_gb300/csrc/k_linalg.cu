@@ -856,8 +856,14 @@ template void launch_gemm<double, double>(const Ctx&, int, int, int, double, Vie
 void launch_gemm_split(const Ctx& cx, int M, int N, int K, View<float> Ahi, View<float> Alo,
                        View<float> Bhi, View<float> Blo, double* C, int64_t ldc,
                        bool upper_only) {
-  gemm_launch<float, double, 4, 4, true>(cx, M, N, K, 1.0, Ahi, Alo, Bhi, Blo, 0.0, C, ldc,
-                                         upper_only ? 2 : 0, 1 << 30);
+  // a 32 x 32 tile when the whole product fits one: a 64 x 64 tile would
+  // spend three quarters of its arithmetic on padding
+  if (std::max(M, N) <= 32)
+    gemm_launch<float, double, 2, 2, true>(cx, M, N, K, 1.0, Ahi, Alo, Bhi, Blo, 0.0, C, ldc,
+                                           upper_only ? 2 : 0, 1 << 30);
+  else
+    gemm_launch<float, double, 4, 4, true>(cx, M, N, K, 1.0, Ahi, Alo, Bhi, Blo, 0.0, C, ldc,
+                                           upper_only ? 2 : 0, 1 << 30);
 }
 
 template <class T>

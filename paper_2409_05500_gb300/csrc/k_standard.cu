@@ -18,7 +18,7 @@ namespace vl {
 namespace {
 
 constexpr int SC_WARPS = 8;  // rows scored per CTA (one warp per row)
-constexpr int RF_TH = 256;   // threads of the refinement CTA (one CTA per row)
+constexpr int RF_TH = 256;   // threads of a refinement CTA (a row is 1-8 CTAs)
 
 // smallest score, its index (lowest among equal scores) and the second
 // smallest score (equal values counted separately)
@@ -106,60 +106,28 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
   }
 }
 
-__device__ __forceinline__ void block_sum2(double& x, double& y, double* red) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    x += __shfl_xor_sync(0xffffffffu, x, o);
-    y += __shfl_xor_sync(0xffffffffu, y, o);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();  // red may still be read from the previous call
-  if (lane == 0) {
-    red[2 * warp] = x;
-    red[2 * warp + 1] = y;
-  }
-  __syncthreads();
-  x = 0.0;
-  y = 0.0;
-  for (int w = 0; w < RF_TH / 32; ++w) {
-    x += red[2 * w];
-    y += red[2 * w + 1];
-  }
-}
-
 // Eq. 4 for output row an (0..u-2): source row a = an, skipping the pick;
-// x_a <- x_a - cov(x_a, x_pick) / var(x_pick) x_pick, with the covariance and
-// variance taken about the means (ddof 0), all in FP64.  Writes the compacted
-// row, idx_next[an] = idx[a] and, when one variable is left, its order entry.
+// x_a <- x_a - (C_a,pick / C_pick,pick) x_pick, where C (u x u) holds the
+// centred cross products of this iteration's data that the measure computed
+// for its correlations, so the ratio is cov(x_a, x_pick) / var(x_pick)
+// (ddof cancels).  FP64.  Writes the compacted row, idx_next[an] = idx[a]
+// and, when one variable is left, its order entry.
 __global__ void __launch_bounds__(RF_TH)
     std_refine_kernel(const double* __restrict__ W, int64_t ldw, int u, int n,
-                      const int* __restrict__ pick, const int32_t* __restrict__ idx,
-                      double* __restrict__ Wn, int64_t ldn, int32_t* __restrict__ idx_next,
-                      int32_t* __restrict__ order, double* __restrict__ gap, int k) {
-  __shared__ double red[2 * RF_TH / 32];
+                      const double* __restrict__ C, const int* __restrict__ pick,
+                      const int32_t* __restrict__ idx, double* __restrict__ Wn, int64_t ldn,
+                      int32_t* __restrict__ idx_next, int32_t* __restrict__ order,
+                      double* __restrict__ gap, int k) {
   const int pk = *pick;
-  const int an = blockIdx.x;
+  const int an = blockIdx.y;
   const int a = an + (an >= pk ? 1 : 0);
+  const double slope = C[(int64_t)a * u + pk] / C[(int64_t)pk * u + pk];
   const double* xa = W + (int64_t)a * ldw;
   const double* xp = W + (int64_t)pk * ldw;
-  double sa = 0.0, sp = 0.0;
-  for (int t = threadIdx.x; t < n; t += RF_TH) {
-    sa += xa[t];
-    sp += xp[t];
-  }
-  block_sum2(sa, sp, red);
-  const double ma = sa / n, mp = sp / n;
-  double cv = 0.0, vr = 0.0;
-  for (int t = threadIdx.x; t < n; t += RF_TH) {
-    const double da = xa[t] - ma, dp = xp[t] - mp;
-    cv = fma(da, dp, cv);
-    vr = fma(dp, dp, vr);
-  }
-  block_sum2(cv, vr, red);
-  const double slope = cv / vr;  // var 0 is reported by the measure as degenerate
   double* dst = Wn + (int64_t)an * ldn;
-  for (int t = threadIdx.x; t < n; t += RF_TH) dst[t] = fma(-slope, xp[t], xa[t]);
-  if (threadIdx.x == 0) {
+  for (int t = blockIdx.x * RF_TH + threadIdx.x; t < n; t += gridDim.x * RF_TH)
+    dst[t] = fma(-slope, xp[t], xa[t]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int32_t orig = idx ? idx[a] : a;
     idx_next[an] = orig;
     if (u == 2) {  // the last variable closes the order
@@ -179,12 +147,13 @@ void launch_std_score_pick(const double* D, int u, double* S, unsigned* counter,
       D, u, S, counter, idx, order, gap, k, pick, st);
 }
 
-void launch_std_refine(const double* W, int64_t ldw, int u, int n, const int* pick,
-                       const int32_t* idx, double* Wn, int64_t ldn, int32_t* idx_next,
-                       int32_t* order, double* gap, int k, cudaStream_t s) {
+void launch_std_refine(const double* W, int64_t ldw, int u, int n, const double* C,
+                       const int* pick, const int32_t* idx, double* Wn, int64_t ldn,
+                       int32_t* idx_next, int32_t* order, double* gap, int k, cudaStream_t s) {
+  const int chunks = std::min(8, std::max(1, (n + 4 * RF_TH - 1) / (4 * RF_TH)));
   note_launch();
-  std_refine_kernel<<<u - 1, RF_TH, 0, s>>>(W, ldw, u, n, pick, idx, Wn, ldn, idx_next, order,
-                                            gap, k);
+  std_refine_kernel<<<dim3(chunks, u - 1), RF_TH, 0, s>>>(W, ldw, u, n, C, pick, idx, Wn, ldn,
+                                                          idx_next, order, gap, k);
 }
 
 }  // namespace vl

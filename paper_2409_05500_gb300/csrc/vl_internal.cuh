@@ -198,14 +198,15 @@ void launch_causal_order(const double* D, int m, void* ws, int32_t* order, doubl
 // Iterative search of Sec. 3 (k_standard.cu).  score_pick: Eq. 3 over the
 // u x u measure D, argmin (ties: lowest index) into *pick, order[k] =
 // idx[pick] (idx NULL: identity), gap[k]; counter: a zeroed device word the
-// kernel re-arms.  refine: Eq. 4 on the pick, rows compacted into Wn (u - 1
-// rows), idx_next; at u == 2 also order[k + 1].
+// kernel re-arms.  refine: Eq. 4 on the pick with the slopes C_a,pick /
+// C_pick,pick of the centred cross products C (u x u), rows compacted into
+// Wn (u - 1 rows), idx_next; at u == 2 also order[k + 1].
 void launch_std_score_pick(const double* D, int u, double* S, unsigned* counter,
                            const int32_t* idx, int32_t* order, double* gap, int k, int* pick,
                            int* st, cudaStream_t s);
-void launch_std_refine(const double* W, int64_t ldw, int u, int n, const int* pick,
-                       const int32_t* idx, double* Wn, int64_t ldn, int32_t* idx_next,
-                       int32_t* order, double* gap, int k, cudaStream_t s);
+void launch_std_refine(const double* W, int64_t ldw, int u, int n, const double* C,
+                       const int* pick, const int32_t* idx, double* Wn, int64_t ldn,
+                       int32_t* idx_next, int32_t* order, double* gap, int k, cudaStream_t s);
 
 // B0 / B_tau helpers (k_fitb.cu)
 template <class T>

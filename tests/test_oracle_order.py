@@ -188,3 +188,21 @@ def test_standard_walk_follows_the_candidates_refinement():
     assert ok and ties == 1
     ok0, _, bad0 = oracle.order_standard_gap_ok(Xs, cand)
     assert not ok0 and bad0 == [0]
+
+
+def test_standard_walk_checks_the_reported_gaps():
+    """The candidate's per-iteration gaps must equal the reference's up to what
+    the allowed D difference explains: the oracle's own gaps pass exactly, a
+    gap off by 0.05 fails at that iteration unless d_tol is large."""
+    inst = synth.make_instance(6, 3000, 1, 91, "uniform", 0.4, 0.3, 0.8, "unif", 0.3)
+    M, E = oracle.var_ols(inst.X, 1)
+    Xs = oracle.standardize(E)
+    od = oracle.order_standard(Xs)
+    own = [int(c) for c in od["order"]]
+    gaps = [oracle.relative_gap(st["scores"]) for st in od["steps"]]
+    assert oracle.order_standard_gap_ok(Xs, own, gaps_cand=gaps) == (True, 0, [])
+    off = list(gaps)
+    off[2] += 0.05
+    ok, ties, bad = oracle.order_standard_gap_ok(Xs, own, gaps_cand=off)
+    assert not ok and bad == [2]
+    assert oracle.order_standard_gap_ok(Xs, own, d_tol=0.5, gaps_cand=off)[0]
