@@ -597,6 +597,9 @@ vl_status vl_reserve(vl_handle h, int m, int n, int p) {
   size_t b = 0;
   b += 8 * (mp * (mp + m) * 2 + 16 * std::max(mm, mp * mp) + (size_t)m * ln * 3);
   b += 8 * (mm * 8 + mpad * ln + (size_t)64 * mm);
+  // pairwise partials of a problem too small to fill one wave: shorter
+  // splits, at most one CTA per SM, 4096 doubles per CTA beyond the m^2 terms
+  b += 8 * (size_t)4096 * h->num_sms;
   DeviceGuard g(h->device);
   return ensure_ws(h, b);
 }

@@ -433,7 +433,11 @@ PairPlan plan_pairwise_slots(int m, int n, int slots, int tts, bool fp64, int nu
   const int Tside = pl.m_pad / TB;
   pl.tiles = Tside * (Tside + 1) / 2;
   const int n_run = ((n + KRUN - 1) / KRUN) * KRUN;
-  const int max_split = std::max(1, n_run / (2 * tts));
+  int max_split = std::max(1, n_run / (2 * tts));
+  // a small problem that does not fill one wave even at this split count gets
+  // shorter splits (down to 4 runs of samples each), up to one CTA per slot
+  if ((long)pl.tiles * max_split < slots)
+    max_split = std::max(max_split, std::min(n_run / (4 * KRUN), (slots + pl.tiles - 1) / pl.tiles));
   int splits = 1;
   double best = -1.0;
   for (int sp = 1; sp <= max_split; ++sp) {
