@@ -41,8 +41,8 @@ SFU_PER_SM_CLK = 32  # ex2 results per SM per clock on this part
 # DRAM bytes per launch of the pairwise kernel at m=400, n=2500 from one ncu
 # capture (profiles/pairwise_f32_finance_m400.md), valid only for the kernel
 # source it was taken on: reported as null once the source changes.
-PAIRWISE_TRAFFIC = {"sha1": "4d3ec53c751b6a66e6b28ff9c9d64373bbd78297",
-                    "bytes": 4911360 + 1792, "m": 400, "n": 2500}
+PAIRWISE_TRAFFIC = {"sha1": "6e7b7d5e2950d3c911d1bf479f1eb1d505723dd8",
+                    "bytes": 4912640 + 1792, "m": 400, "n": 2500}
 MAX_SM_MHZ = 2070.0
 
 
@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-standard", action="store_true",
                     help="skip timing the iterative search of Section 3")
+    ap.add_argument("--profile-standard", action="store_true",
+                    help="only run the iterative search of Section 3 once, between "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off), and exit")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batched", action="store_true",
                     help="also time the 256-series mixed-size batch (vl_fit_batched)")
@@ -506,8 +509,44 @@ def run_reference(args):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_standard(args):
+    """One warm call of the iterative search, then one call bracketed by
+    cudaProfilerStart/Stop: a profiler started with profile-from-start off sees
+    exactly the launches of one search."""
+    import torch
+
+    import synth
+    import paper_2409_05500_gb300 as vl
+
+    inst = synth.make_config(args.workload)
+    m, n, p = inst.m, inst.n, inst.p
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = vl.Handle(0, stream)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    M = torch.empty((p, m, m), **f64)
+    E = torch.empty((m, n - p), **f64)
+    vl.vl_var_fit(h, torch.from_numpy(inst.X).cuda(), p, args.prec, M, E)
+    order = torch.empty(m, dtype=torch.int32, device="cuda")
+    vl.vl_causal_order_standard(h, E, args.prec, order)
+    h.sync()
+    l0 = vl.kernel_launches()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    vl.vl_causal_order_standard(h, E, args.prec, order)
+    h.sync()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    h.close()
+    return {"profiled": "vl_causal_order_standard", "workload": workload_desc(inst, args.workload),
+            "precision": args.prec, "launches": vl.kernel_launches() - l0}
+
+
 def main():
     args = parse()
+    if args.profile_standard:
+        print(json.dumps(profile_standard(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -323,6 +323,39 @@ def test_standard_first_pick_is_algorithm1_first_pick(vl, h):
         assert o1[0].item() == o2[0].item()
 
 
+def test_standard_order_replays_from_a_cuda_graph(vl):
+    """After one call of a shape the iterative search allocates nothing and
+    never waits on the host (the picks stay on the device): captured into one
+    CUDA graph and replayed on other data of that shape, it gives the eager
+    results."""
+    E, _, _ = _std_case("fmri")
+    rng = np.random.default_rng(11)
+    Eb = E + 0.05 * rng.standard_normal(E.shape)
+    m = E.shape[0]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = vl.Handle(stream=stream)
+        Et = torch.from_numpy(np.ascontiguousarray(E)).cuda()
+        order = torch.empty(m, dtype=torch.int32, device="cuda")
+        gap = torch.empty(m, dtype=torch.float64, device="cuda")
+        vl.vl_causal_order_standard(h, Et, "mixed", order, gap)
+        h.sync()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            vl.vl_causal_order_standard(h, Et, "mixed", order, gap)
+        for En in (E, Eb):
+            Et.copy_(torch.from_numpy(np.ascontiguousarray(En)))
+            g.replay()
+            stream.synchronize()
+            o2 = torch.empty_like(order)
+            g2 = torch.empty_like(gap)
+            vl.vl_causal_order_standard(h, torch.from_numpy(np.ascontiguousarray(En)).cuda(),
+                                        "mixed", o2, g2)
+            h.sync()
+            assert torch.equal(order, o2) and torch.equal(gap, g2)
+        h.close()
+
+
 def test_standard_order_reports_degeneracy_after_refinement(vl, h):
     """x_2 = x_0 + x_1: no pair is collinear, but once one variable is
     removed by Eq. 4 the other two are, and the next measure reports it."""
