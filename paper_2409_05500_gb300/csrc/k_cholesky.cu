@@ -438,30 +438,29 @@ __global__ void __launch_bounds__(CTH, 1)
     __syncthreads();
     if (pf && tid == 0) pf[8 * k + 1] = gtime();
     // (c) panel k-1 on block column k of the owned row blocks below k, and on
-    //     diagonal block k+1 if owned
-    if (k >= 1) {
-      int ntile = 0;
-      for (int b = jb; b < nblk; b += cl) ++ntile;
-      const int ntask = 4 * (ntile + (next_owner ? 1 : 0));
-      for (int t = warp; t < ntask; t += nwarp) {
-        const int tile = t >> 2, qr = t & 3;
-        const int b = tile < ntile ? jb + tile * cl : k + 1;
-        const int j = tile < ntile ? k : k + 1;
-        float* X = blk(b);
-        const int ld = Layout::ldb(b);
-        tile_rows(X + j * CB, ld, X + (k - 1) * CB, ld, gbuf + (size_t)(j * CB - gbase) * RS, RS,
-                  min(CB, n - j * CB), qr * 8, qr * 8 + 8);
-      }
-      __syncthreads();
-    }
-    if (pf && tid == 0) pf[8 * k + 2] = gtime();
-    // (d) panel rows of block column k for the owned row blocks below k
+    //     diagonal block k+1 if owned; (d) panel rows of block column k for the
+    //     owned row blocks below k.  Both act row by row, so the warp that
+    //     updates 8 rows in (c) forms the same 8 panel rows in (d) right after,
+    //     with no CTA barrier between the two.
     {
       int ntile = 0;
       for (int b = jb; b < nblk; b += cl) ++ntile;
-      for (int t = warp; t < 4 * ntile; t += nwarp) {
-        const int b = jb + (t >> 2) * cl, qr = t & 3;
-        panel_tile_rows(blk(b) + k * CB, Layout::ldb(b), linv, qr * 8, qr * 8 + 8);
+      const int ntask = 4 * (ntile + (k >= 1 && next_owner ? 1 : 0));
+      for (int t = warp; t < ntask; t += nwarp) {
+        const int tile = t >> 2, qr = t & 3;
+        if (k >= 1) {
+          const int b = tile < ntile ? jb + tile * cl : k + 1;
+          const int j = tile < ntile ? k : k + 1;
+          float* X = blk(b);
+          const int ld = Layout::ldb(b);
+          tile_rows(X + j * CB, ld, X + (k - 1) * CB, ld, gbuf + (size_t)(j * CB - gbase) * RS,
+                    RS, min(CB, n - j * CB), qr * 8, qr * 8 + 8);
+        }
+        if (tile < ntile) {
+          __syncwarp();
+          const int b = jb + tile * cl;
+          panel_tile_rows(blk(b) + k * CB, Layout::ldb(b), linv, qr * 8, qr * 8 + 8);
+        }
       }
       __syncthreads();
     }
