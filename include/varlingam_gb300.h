@@ -181,7 +181,7 @@ vl_status vl_causal_order_noalloc(void* cuda_stream, const double* D, int m, int
  *         smallest scores of iteration k, as in vl_causal_order (+inf last).
  * Runs asynchronously on the handle's stream with no host synchronisation
  * (the picks stay on the device); its buffers are the handle's series
- * buffers (shared with vl_fit, 2 m n_eff + 2 m^2 + 3 m doubles) and workspace,
+ * buffers (shared with vl_fit, about 2 m n_eff + 2 m^2 + 2 m doubles) and workspace,
  * so after a first call of the same or larger size it allocates nothing.
  * Device errors (degenerate or non-finite data at any iteration) surface at
  * vl_sync().  Requires 2 <= m <= VL_MAX_M, n_eff >= 2.
