@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(TB / MTI * 16, MINB)
                         const float* __restrict__ c32, float* __restrict__ part) {
   constexpr int NT = TB / MTI * 16;
   extern __shared__ __align__(16) float pw_smem[];
-  float(*sx)[TTS][2 * TB] = reinterpret_cast<float(*)[TTS][2 * TB]>(pw_smem);  // [2][TTS][64]
+  float(*sx)[TTS][2 * TB] = reinterpret_cast<float(*)[TTS][2 * TB]>(pw_smem);  // [3][TTS][64]
   int I, J;
   tile_coords(blockIdx.x, T, I, J);
   const int split = blockIdx.y;
@@ -209,17 +209,21 @@ __global__ void __launch_bounds__(TB / MTI * 16, MINB)
     cp_async_commit();
   };
 
-  int buf = 0;
-  if (t0 < t1) load_stage(0, t0);
-  for (int tb = t0; tb < t1; tb += TTS) {
+  // three-stage ring: stage s+2 is copied while stage s is consumed, and the
+  // one barrier per stage both publishes stage s and frees the buffer of
+  // stage s-1 for the copy of stage s+2
+  const int nst = t1 > t0 ? (t1 - t0 + TTS - 1) / TTS : 0;
+  if (nst > 0) load_stage(0, t0);
+  if (nst > 1) load_stage(1, t0 + TTS);
+  for (int st = 0; st < nst; ++st) {
+    const int tb = t0 + st * TTS, buf = st % 3;
     const int rows = min(TTS, t1 - tb);
-    if (tb + TTS < t1) {
-      load_stage(buf ^ 1, tb + TTS);
+    if (st + 1 < nst)
       cp_async_wait<1>();
-    } else {
+    else
       cp_async_wait<0>();
-    }
     __syncthreads();
+    if (st + 2 < nst) load_stage((st + 2) % 3, tb + 2 * TTS);
     for (int r0 = 0; active && r0 < rows; r0 += KRUN) {
 #pragma unroll
       for (int k = 0; k < KRUN; ++k) {
@@ -242,8 +246,6 @@ __global__ void __launch_bounds__(TB / MTI * 16, MINB)
 #pragma unroll
       for (int k = 0; k < 2 * MTI; ++k) end_run2(q[k]);
     }
-    __syncthreads();
-    buf ^= 1;
   }
 
   // partials of this split as exact double-float pairs (sum, -comp):
@@ -477,7 +479,7 @@ void launch_pairwise_f32_cfg(const float* xt, const PairPlan& pl, const float* r
                              const float* c32, float* part, cudaStream_t s) {
   const int n_run = ((pl.n + KRUN - 1) / KRUN) * KRUN;
   dim3 grid(pl.tiles, pl.splits);
-  const size_t smem = sizeof(float) * 2 * TTS * 2 * TB;  // two stages of TTS x 64 samples
+  const size_t smem = sizeof(float) * 3 * TTS * 2 * TB;  // three stages of TTS x 64 samples
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(pairwise_f32_kernel<MTI, TTS, MINB>,
