@@ -65,3 +65,49 @@ def test_create_fails_cleanly_without_device(lib):
     lib.vl_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, ctypes.c_size_t]
     assert lib.vl_create(ctypes.byref(h), 0, None, 0) == 6  # VL_ERR_CUDA
     assert not h.value
+
+
+def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
+    """Each declared entry point that takes a handle answers VL_ERR_ARG (1) for
+    a NULL handle before touching a device; the handle-free ordering entry
+    point answers its argument, shape and size errors the same way."""
+    P, I, I64, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    calls = {
+        "vl_destroy": ([P], [None]),
+        "vl_set_stream": ([P, P], [None, None]),
+        "vl_reserve": ([P, I, I, I], [None, 10, 100, 1]),
+        "vl_sync": ([P], [None]),
+        "vl_profile_events": ([P, P, P], [None, None, None]),
+        "vl_var_fit": ([P, P, I64, I, I, I, I, P, P], [None, None, 100, 10, 100, 1, 1, None, None]),
+        "vl_pairwise_measure": ([P, P, I64, I, I, I, P, P, P],
+                                [None, None, 100, 10, 100, 1, None, None, None]),
+        "vl_causal_order": ([P, P, I, P, P], [None, None, 10, None, None]),
+        "vl_causal_order_standard": ([P, P, I64, I, I, I, P, P],
+                                     [None, None, 100, 10, 100, 1, None, None]),
+        "vl_fit_b": ([P, P, I64, I, I, P, P, I, I, P, P],
+                     [None, None, 100, 10, 100, None, None, 1, 1, None, None]),
+        "vl_fit": ([P, P, I64, I, I, I, I, P, P, P, P, P],
+                   [None, None, 100, 10, 100, 1, 1, None, None, None, None, None]),
+        "vl_fit_batched": ([P, P, I, I, P], [None, None, 1, 1, None]),
+    }
+    handle_calls = [n for n in declared_functions()
+                    if n not in ("vl_create", "vl_kernel_launches", "vl_last_error",
+                                 "vl_causal_order_noalloc")]
+    assert sorted(handle_calls) == sorted(calls)
+    lib.vl_kernel_launches.restype = ctypes.c_ulonglong
+    lib.vl_kernel_launches.argtypes = []
+    launches0 = lib.vl_kernel_launches()
+    for name, (argtypes, args) in calls.items():
+        f = getattr(lib, name)
+        f.argtypes = argtypes
+        f.restype = I
+        assert f(*args) == 1, name
+    f = lib.vl_causal_order_noalloc
+    f.argtypes = [P, P, I, P, P]
+    f.restype = I
+    buf = (ctypes.c_double * 4)()
+    order = (ctypes.c_int32 * 4)()
+    assert f(None, None, 4, None, None) == 1              # VL_ERR_ARG
+    assert f(None, ctypes.addressof(buf), 0, ctypes.addressof(order), None) == 2   # VL_ERR_SHAPE
+    assert f(None, ctypes.addressof(buf), 513, ctypes.addressof(order), None) == 9  # UNSUPPORTED
+    assert lib.vl_kernel_launches() == launches0          # none of these launched anything
