@@ -232,11 +232,15 @@ typedef struct {
 
 /*
  * The whole method (steps 1-4 above) for `count` independent series of
- * possibly different (m, n, p), issued as one sequence of batched kernels on
- * the handle's stream.  inst and inst_status are HOST arrays of length
- * count; inst_status[k] receives the instance's own status after the call
- * has completed (the call synchronises the stream).  Returns the first
- * non-OK instance status, or a host-side error.
+ * possibly different (m, n, p).  The series are dealt, largest first, to a
+ * pool of up to 8 streams forked from the handle's stream and joined back
+ * into it; each stream has its own workspace.  inst and inst_status are HOST
+ * arrays of length count; inst_status[k] receives the instance's own status
+ * after the call has completed (the call synchronises the stream).  An
+ * instance that fails the host checks reports that error and is skipped; when
+ * the call fails as a whole (workspace or stream creation, a CUDA error),
+ * every other instance reports that error.  Returns the first non-OK
+ * instance status, or a host-side error.
  */
 vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_precision prec,
                          vl_status* inst_status);

@@ -223,8 +223,11 @@ def vl_fit_batched(h: Handle, instances: Sequence[Dict[str, torch.Tensor]], prec
                              d["order"].data_ptr(), d["B0"].data_ptr(), d["Btau"].data_ptr(),
                              d["M"].data_ptr(), d["D"].data_ptr() if d.get("D") is not None else None)
     status = (ctypes.c_int * len(instances))()
-    _lib.vl_fit_batched(h.h, arr, len(instances), PRECISIONS[prec], status)
-    return [int(s) for s in status]
+    code = _lib.vl_fit_batched(h.h, arr, len(instances), PRECISIONS[prec], status)
+    out = [int(s) for s in status]
+    if code != VL_OK and all(s == VL_OK for s in out):  # a failure of the call itself
+        h.check(code, "vl_fit_batched")
+    return out
 
 
 # ------------------------------------------------------------ conveniences

@@ -468,6 +468,7 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
       h->bstatus_cap = 0;
       if (cudaMalloc(&h->bstatus, sizeof(int) * count) != cudaSuccess) {
         cudaGetLastError();
+        for (int k : idx) inst_status[k] = VL_ERR_NOMEM;
         return fail(h, VL_ERR_NOMEM, "vl_fit_batched: status array allocation failed");
       }
       h->bstatus_cap = count;
@@ -487,7 +488,10 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
       s = grow(h, &ps.ws, &ps.ws_cap, ws_need, ps.stream);
       if (s == VL_OK) s = grow(h, &ps.buf, &ps.buf_cap, buf_need, ps.stream);
     }
-    if (s != VL_OK) return s;
+    if (s != VL_OK) {  // nothing ran: every valid instance reports the call's error
+      for (int k : idx) inst_status[k] = s;
+      return s;
+    }
     cudaMemsetAsync(h->bstatus, 0, sizeof(int) * count, h->stream);
     // fork: every pool stream waits for the handle stream
     cudaEvent_t fork = h->pool[0].done;
@@ -514,8 +518,10 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
     cudaError_t e = cudaMemcpyAsync(dev.data(), h->bstatus, sizeof(int) * count,
                                     cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess)
+    if (e != cudaSuccess) {
+      for (int k : idx) inst_status[k] = VL_ERR_CUDA;
       return fail(h, VL_ERR_CUDA, std::string("vl_fit_batched: ") + cudaGetErrorString(e));
+    }
     for (int k : idx)
       if (inst_status[k] == VL_OK && dev[k] != 0) inst_status[k] = (vl_status)dev[k];
   }
