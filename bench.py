@@ -23,6 +23,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -133,7 +134,9 @@ def cpu_baseline_all_cores(inst, m_s):
 class ClockSampler:
     def __init__(self, dev):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{dev}.csv")
+        # raw samples: VL_CLOCKS_DIR if set, else the system temporary directory
+        out_dir = os.environ.get("VL_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_dev{dev}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
