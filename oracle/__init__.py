@@ -10,6 +10,8 @@ paper by eye.
 Contents (all in :mod:`oracle.fp64`):
 
 * ``var_ols``            VAR(p) least squares with intercept (Section 4.1).
+* ``var_select``         lag order by AIC / BIC / HQ on a common sample (a reading:
+                         the paper takes p as given).
 * ``standardize``        zero mean, unit variance per variable (Section 3, step 1).
 * ``entropy``            maximum-entropy approximation H(u) (Section 3, step 3;
                          the constants are pinned in ``entropy_constants``).
@@ -57,5 +59,6 @@ from .fp64 import (  # noqa: F401
     scores_over,
     standardize,
     var_ols,
+    var_select,
     varlingam,
 )

@@ -69,6 +69,35 @@ def var_ols(X: np.ndarray, p: int) -> Tuple[np.ndarray, np.ndarray]:
     return M, np.ascontiguousarray(E)
 
 
+def var_select(X: np.ndarray, p_max: int, criterion: str = "bic") -> Dict[str, object]:
+    """Lag order of the VAR by an information criterion (the paper takes p as
+    given, Sec. 4.1; the reading follows the standard VAR practice, Lutkepohl,
+    New Introduction to Multiple Time Series Analysis, Sec. 4.3).
+
+    Every candidate p = 1..p_max is fitted by :func:`var_ols` on the same
+    T = n - p_max equations (t = p_max .. n-1), so the criteria compare fits of
+    the same data.  With the ML residual covariance S(p) = E E^T / T:
+        AIC(p) = ln det S(p) + 2 p m^2 / T
+        BIC(p) = ln det S(p) + ln(T) p m^2 / T
+        HQ(p)  = ln det S(p) + 2 ln(ln T) p m^2 / T
+    (the m intercepts are common to every p and left out).  The smallest
+    value wins; ties pick the smaller p."""
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    T = n - p_max
+    pen = {"aic": 2.0, "bic": math.log(T), "hq": 2.0 * math.log(math.log(T))}[criterion]
+    values = []
+    for p in range(1, p_max + 1):
+        _, E = var_ols(X[:, p_max - p:], p)
+        S = E @ E.T / T
+        sign, logdet = np.linalg.slogdet(S)
+        if sign <= 0:
+            raise ValueError("residual covariance is not positive definite")
+        values.append(logdet + pen * p * m * m / T)
+    best = 1 + min(range(p_max), key=lambda i: (values[i], i))
+    return {"p": best, "values": values, "T": T}
+
+
 # ------------------------------------------------------ pairwise measure
 def standardize(X: np.ndarray) -> np.ndarray:
     """Zero mean and unit variance per variable (Section 3, step 1), with the

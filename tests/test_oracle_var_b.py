@@ -67,3 +67,43 @@ def test_full_pipeline_heuristic_recovers_b0():
     inst = synth.make_instance(6, 50_000, 1, 17, "uniform", 0.4, 0.3, 0.7, "unif", 0.5)
     out = oracle.varlingam(inst.X, 1)
     assert np.max(np.abs(out["B0"] - inst.B0)) < 0.05
+
+
+def test_lag_selection_recovers_the_true_order_at_large_n():
+    """BIC is consistent: on long series of VAR(1), VAR(2) and VAR(3)
+    processes with clear lag coefficients it selects the generating p."""
+    for p_true, seed in ((1, 11), (2, 12), (3, 13)):
+        inst = synth.make_instance(4, 20000, p_true, seed, "laplace", 0.3, 0.2, 0.5, "unif", 0.8,
+                                   var_lo=0.2, var_hi=0.4)
+        sel = oracle.var_select(inst.X, 5, "bic")
+        assert sel["p"] == p_true, (p_true, sel["values"])
+
+
+def test_lag_selection_invariances_and_penalty_order():
+    """Scaling the data by c shifts every criterion by exactly 2 m ln c and
+    permuting the variables changes none, so neither changes the choice; the
+    penalties order AIC <= HQ <= BIC (T > 15), so the selected lags order the
+    other way; the candidate with p = p_max is the plain fit on all rows."""
+    rng = np.random.default_rng(4)
+    inst = synth.make_instance(5, 400, 2, 21, "uniform", 0.3, 0.1, 0.5, "unif", 0.7)
+    X = inst.X
+    base = oracle.var_select(X, 4, "aic")
+    c = 3.7
+    scaled = oracle.var_select(c * X, 4, "aic")
+    np.testing.assert_allclose(np.array(scaled["values"]) - np.array(base["values"]),
+                               2 * 5 * np.log(c), rtol=0, atol=1e-9)
+    assert scaled["p"] == base["p"]
+    perm = rng.permutation(5)
+    np.testing.assert_allclose(oracle.var_select(X[perm], 4, "aic")["values"], base["values"],
+                               rtol=0, atol=1e-9)
+    for k in range(20):
+        Xr = synth.make_instance(3, 120, 1 + k % 3, 100 + k, "laplace", 0.3, 0.1, 0.5, "unif",
+                                 0.6).X
+        pa = oracle.var_select(Xr, 4, "aic")["p"]
+        ph = oracle.var_select(Xr, 4, "hq")["p"]
+        pb = oracle.var_select(Xr, 4, "bic")["p"]
+        assert pb <= ph <= pa
+    M, E = oracle.var_ols(X, 4)
+    S = E @ E.T / E.shape[1]
+    full = np.linalg.slogdet(S)[1] + np.log(X.shape[1] - 4) * 4 * 25 / (X.shape[1] - 4)
+    assert abs(oracle.var_select(X, 4, "bic")["values"][3] - full) < 1e-9
