@@ -11,6 +11,8 @@
  *   3. order the variables by m greedy argmins of Eq. 3 over that static
  *      matrix                                                  (Algorithm 1)
  *   4. estimate B0 from the order and B_tau = (I - B0) M_tau       (Sec. 4)
+ * and, for comparison, the iterative search that step 3 approximates, which
+ * re-measures the remaining variables after every pick      (Sec. 3, Eq. 4)
  *
  * Conventions shared by every call:
  *   - All array arguments are DEVICE pointers owned by the caller; the library
@@ -54,7 +56,7 @@ typedef enum {
   VL_ERR_CUDA = 6,        /* a CUDA runtime call failed                         */
   VL_ERR_NOMEM = 7,       /* workspace allocation failed                        */
   VL_ERR_TIMEOUT = 8,     /* a bounded device wait gave up                      */
-  VL_ERR_UNSUPPORTED = 9  /* size beyond this build's limits                    */
+  VL_ERR_UNSUPPORTED = 9  /* size beyond the library's fixed limits            */
 } vl_status;
 
 typedef enum { VL_PREC_FP64 = 0, VL_PREC_MIXED = 1 } vl_precision;
