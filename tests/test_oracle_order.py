@@ -206,3 +206,22 @@ def test_standard_walk_checks_the_reported_gaps():
     ok, ties, bad = oracle.order_standard_gap_ok(Xs, own, gaps_cand=off)
     assert not ok and bad == [2]
     assert oracle.order_standard_gap_ok(Xs, own, d_tol=0.5, gaps_cand=off)[0]
+
+
+def test_refinement_recovers_the_generating_noise():
+    """Eq. 4 against a known linear model x1 = e1, x2 = 0.8 x1 + e2,
+    x3 = 0.5 x2 + e3 (independent uniform shocks): the residual of x2 on x1 is
+    e2 and that of x3 on x1 is 0.5 e2 + e3 (up to sampling), and the iterative
+    search orders the chain causes first."""
+    rng = np.random.default_rng(17)
+    n = 50000
+    e = rng.uniform(-1, 1, size=(3, n))
+    x1 = e[0]
+    x2 = 0.8 * x1 + e[1]
+    x3 = 0.5 * x2 + e[2]
+    X = np.stack([x1, x2, x3])
+    r2 = oracle.residual(x2, x1)
+    r3 = oracle.residual(x3, x1)
+    assert np.corrcoef(r2, e[1])[0, 1] > 0.9999
+    assert np.corrcoef(r3, 0.5 * e[1] + e[2])[0, 1] > 0.9999
+    assert [int(c) for c in oracle.order_standard(oracle.standardize(X))["order"]] == [0, 1, 2]
