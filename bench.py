@@ -40,8 +40,8 @@ UNIT = "pair-samples/s"
 SFU_SLOTS_PER_PAIR_SAMPLE = 4.25
 SFU_PER_SM_CLK = 32  # ex2 results per SM per clock on this part
 # DRAM bytes per launch of the pairwise kernel at m=400, n=2500 from one ncu
-# capture (profiles/pairwise_f32_finance_m400.md), valid only for the kernel
-# source it was taken on: reported as null once the source changes.
+# capture, valid only for the kernel source it was taken on: reported as null
+# once the source changes.
 PAIRWISE_TRAFFIC = {"sha1": "8f1fcecb8607f08501843ba60ef24191cfad1d2d",
                     "bytes": 4913408 + 2816, "m": 400, "n": 2500}
 MAX_SM_MHZ = 2070.0

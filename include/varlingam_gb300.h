@@ -138,10 +138,11 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
 /*
  * Allocation-free variant of vl_causal_order (same search, same results).
  * This entry point has no counterpart in the paper; it exists for callers that
- * cannot allocate device memory when they need the ordering: code running
- * under CUDA stream capture (where cudaMalloc is not allowed), frameworks
- * that own all device memory through their own allocator, and latency-bound
- * loops where an allocation would stall the device.  It needs no handle and
+ * cannot allocate device memory when they need the ordering: frameworks and
+ * serving runtimes that own all device memory through their own pooling
+ * allocator (a stray cudaMalloc would bypass their accounting, or fail when
+ * the pool has already taken the free memory), and latency-bound loops that
+ * must not pay for an allocation, which synchronises the device.  It needs no handle and
  * allocates nothing: its scratch is a fixed device array inside the library
  * (about 2.1 MB, held on every GPU that loads the library until the process
  * exits), so it accepts 1 <= m <= VL_NOALLOC_MAX_M and returns

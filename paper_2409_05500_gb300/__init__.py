@@ -35,8 +35,8 @@ PRECISIONS = {"fp64": VL_PREC_FP64, "mixed": VL_PREC_MIXED}
 
 EXPORTED = ("vl_create", "vl_destroy", "vl_set_stream", "vl_reserve", "vl_sync",
             "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_fit", "vl_var_fit",
-            "vl_pairwise_measure", "vl_causal_order", "vl_causal_order_noalloc", "vl_fit_b",
-            "vl_fit_batched")
+            "vl_pairwise_measure", "vl_causal_order", "vl_causal_order_noalloc",
+            "vl_causal_order_standard", "vl_fit_b", "vl_fit_batched")
 
 
 class VLError(RuntimeError):

@@ -76,7 +76,33 @@ def build(verbose: bool = False, extra_flags=None) -> str:
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link of libvarlingam_gb300.so failed")
+    _build_c_example(nvcc, objs)
     return LIB
+
+
+def _build_c_example(nvcc: str, deps) -> None:
+    """The README's C example (tests/c/readme_example.c), compiled with the
+    host C compiler against include/ and linked with the library, so that a
+    test can run it as a plain C program."""
+    src = os.path.join(ROOT, "tests", "c", "readme_example.c")
+    exe = os.path.join(BUILD, "readme_example")
+    if not os.path.exists(src) or not _stale(exe, [src, LIB] + list(deps)):
+        return
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        raise RuntimeError("no C compiler found for tests/c/readme_example.c")
+    cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    libdir = os.path.join(cuda_home, "lib64")
+    if not os.path.isdir(libdir):
+        libdir = os.path.join(cuda_home, "lib")
+    cmd = [cc, "-O2", "-std=c11", "-Wall", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(cuda_home, "include"), src, "-o", exe, "-L", HERE,
+           "-lvarlingam_gb300", "-L", libdir, "-lcudart", "-Wl,-rpath,$ORIGIN/..",
+           "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
+        raise RuntimeError("build of tests/c/readme_example.c failed")
 
 
 if __name__ == "__main__":

@@ -349,7 +349,12 @@ extern "C" vl_status vl_causal_order_noalloc(void* cuda_stream, const double* D,
     scratch = g_noalloc_ptr[dev];
   }
   if (order_ws_bytes(m) > kNoallocBytes) return VL_ERR_UNSUPPORTED;
+  // an error the caller left pending is not this call's: report only an
+  // error that the launches below raise (and clear only that one)
+  const cudaError_t before = cudaPeekAtLastError();
   launch_causal_order(D, m, scratch, order, gap, nullptr, static_cast<cudaStream_t>(cuda_stream));
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? VL_OK : VL_ERR_CUDA;
+  const cudaError_t after = cudaPeekAtLastError();
+  if (after == cudaSuccess || after == before) return VL_OK;
+  cudaGetLastError();
+  return VL_ERR_CUDA;
 }

@@ -1,10 +1,11 @@
 """The allocation-free ordering entry point against the regular one.
 
 vl_causal_order_noalloc serves callers that cannot allocate device memory at
-the moment they need the causal order: code running under CUDA stream capture
-(cudaMalloc is not allowed there), frameworks that own all device memory
-through their own allocator, and allocation-free inner loops.  It keeps its
-scratch in a fixed device array inside the library instead of a workspace.
+the moment they need the causal order: frameworks and serving runtimes that own
+all device memory through their own pooling allocator, and latency-bound loops
+that must not pay for the device synchronisation an allocation implies.  It
+keeps its scratch in a fixed device array inside the library instead of a
+workspace.
 Its results must equal those of vl_causal_order.  This file is named so that
 pytest collects it last.
 """
@@ -29,9 +30,10 @@ def _regular(vl, h, D):
 def test_noalloc_order_matches_regular_entry_on_consecutive_calls(vl):
     h = vl.Handle(0)
     rng = np.random.default_rng(2024)
-    # two calls in a row on one scratch array: the second is smaller, so it
-    # runs over what the first one left behind
-    for m in (400, 37):
+    # calls in a row on one scratch array: each later one is smaller, so it
+    # runs over what the earlier ones left behind; m = 512 fills the array
+    # exactly
+    for m in (512, 400, 37):
         A = rng.normal(size=(m, m))
         D = torch.from_numpy(A - A.T).cuda()
         ref_order, ref_gap = _regular(vl, h, D)
