@@ -114,10 +114,17 @@ def sampled_record(X, p, meas, b0_route, seed, n_sample=N_SAMPLE):
     }
 
 
+def _batched_instance(k):
+    """Series k of synth.make_batched(256, seed 2409055 + 4000), drawn alone."""
+    seed = synth.config_seed(4)
+    m, n, p, noise, _ = synth.draw_batched_shapes(256, seed)[k]
+    return synth.make_instance(m, n, p, seed + 1 + k, noise, synth.batched_edge_prob(m),
+                               0.1, 0.5, "unif", 0.8)
+
+
 def _batched_one(k):
     """Worker: the whole oracle on series k of the 256-series batch."""
-    insts = synth.make_batched(256, synth.config_seed(4))
-    inst = insts[k]
+    inst = _batched_instance(k)
     M, E = oracle.var_ols(inst.X, inst.p)
     meas = oracle.pairwise_measure(oracle.standardize(E))
     rec = sampled_record(inst.X, inst.p, meas, oracle.b0_ols, inst.seed)

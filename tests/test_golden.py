@@ -49,3 +49,41 @@ def test_oracle_reproduces_its_stored_small_workload_values():
     assert [int(c) for c in std["order"]] == g["order_standard"]
     gaps = [oracle.relative_gap(st["scores"]) for st in std["steps"][:-1]]
     np.testing.assert_allclose(gaps, g["gaps_standard"], rtol=1e-7)
+
+
+def _sampled(name):
+    import gzip
+
+    with gzip.open(os.path.join(GOLDEN, name), "rt") as f:
+        return json.load(f)
+
+
+def test_stored_batch_values_are_the_oracles():
+    """The stored values of the 256-series batch (written by make_golden.py
+    from the oracle) for the three cheapest series, recomputed here: the
+    fixture holds the oracle's order, gaps and samples."""
+    import sys
+
+    sys.path.insert(0, GOLDEN)
+    import make_golden
+
+    gold = _sampled("batched_oracle.json.gz")["series"]
+    assert len(gold) == 256
+    cheapest = sorted(range(256), key=lambda k: gold[k]["m"] ** 2 * gold[k]["n"])[:3]
+    for k in cheapest:
+        rec = make_golden._batched_one(k)
+        g = gold[k]
+        assert rec["order"] == g["order"]
+        np.testing.assert_allclose(rec["gaps"], g["gaps"], rtol=1e-9, atol=1e-15)
+        for key in ("Ex", "D", "Er", "M", "B0", "Btau"):
+            np.testing.assert_allclose(np.array(rec[key], dtype=float), np.array(g[key], dtype=float),
+                                       rtol=1e-10, atol=1e-13, err_msg=key)
+
+
+def test_stored_stretch_values_are_consistent():
+    for m in (800, 1600):
+        g = _sampled(f"stretch_m{m}_oracle.json.gz")["series"][0]
+        assert g["m"] == m and g["n"] == 5000 and sorted(g["order"]) == list(range(m))
+        assert len(g["gaps"]) == m - 1 and len(g["Ex"]) == m
+        # D is antisymmetric: every sampled entry and the stored maximum agree in size
+        assert max(abs(v) for _, _, v in g["D"]) <= g["D_maxabs"] * (1 + 1e-12)
