@@ -32,19 +32,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pair-samples/s of pairwise measure; end-to-end ms at m=400 (mixed vs FP64)"
 UNIT = "pair-samples/s"
-# Roofline of the pairwise kernel: the special-function unit (MUFU).  Per
-# pair-sample the method needs, for each of the two residuals, two
-# exponentials (e^{-2|u|} for log cosh, e^{-u^2/2}) and, amortised over a
-# 16-sample run, one logarithm, which issues at half the exponential rate:
-# 2 x (2 + 2/16) = 4.25 exponential-equivalent SFU slots.
-SFU_SLOTS_PER_PAIR_SAMPLE = 4.25
-SFU_PER_SM_CLK = 32  # ex2 results per SM per clock on this part
+# Roofline of the pairwise kernel: the special-function unit (MUFU).  The
+# method's own count (the algorithmic work): per pair-sample, two residuals x
+# three transcendentals (e^{-2|u|}, log1p, e^{-u^2/2}) = 6 SFU operations.
+# The kernel issues fewer: the logarithms of 16 samples are taken at once
+# from their product (one lg2 per 16 samples, at half the ex2 rate), so it
+# issues 2 x (2 + 2/16) = 4.25 ex2-equivalent slots per pair-sample.
+MUFU_PER_PAIR_SAMPLE = 6
+SFU_SLOTS_ISSUED = 4.25
+# Nominal exponential rate of this part: 32 ex2 results per SM per clock
+# (Blackwell Ultra doubles the SFU exponential throughput of Blackwell's 16);
+# the run also measures it (vl_sfu_rate) and reports both.
+SFU_NOMINAL_PER_SM_CLK = 32
+MAX_SM_MHZ = 2070.0
 # DRAM bytes per launch of the pairwise kernel at m=400, n=2500 from one ncu
 # capture, valid only for the kernel source it was taken on: reported as null
 # once the source changes.
 PAIRWISE_TRAFFIC = {"sha1": "8f1fcecb8607f08501843ba60ef24191cfad1d2d",
                     "bytes": 4913408 + 2816, "m": 400, "n": 2500}
-MAX_SM_MHZ = 2070.0
 
 
 def parse():
@@ -63,8 +68,8 @@ def parse():
                     help="only run the iterative search of Section 3 once, between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off), and exit")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--batched", action="store_true",
-                    help="also time the 256-series mixed-size batch (vl_fit_batched)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip timing the 256-series mixed-size batch")
     return ap.parse_args()
 
 
@@ -273,6 +278,8 @@ def run_ours(args, rank, world):
         """The fused step captured once into a CUDA graph (the library is
         capture-safe after one call of a shape) and replayed K times, the L2
         flush between replays outside the graph."""
+        fused(prec, X)  # sizes the workspace outside the capture
+        h.sync()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             fused(prec, X)
@@ -371,10 +378,20 @@ def run_ours(args, rank, world):
                     "same_first_pick": bool(so[0].item() == out["order"][0].item())}
 
     # FP64 GPU comparison path (same steps, every kernel in FP64)
+    # the same step on the plain FP64 GPU path and with the certified
+    # ordering, both as graph replays like the headline
     fp64_ms = None
+    certified = None
     if not args.no_fp64_compare and args.prec == "mixed":
-        ms64, _, _ = timed("fp64", max(3, min(5, args.steps)), 1)
-        fp64_ms = sum(ms64) / len(ms64)
+        with torch.cuda.stream(stream):
+            fp64_ms = statistics.median(timed_graph("fp64", 3, 1))
+    if args.prec == "mixed":
+        with torch.cuda.stream(stream):
+            mc = timed_graph("mixed_certified", max(3, min(20, args.steps)), 2)
+        st = vl.fit(h, X, p, prec="mixed_certified", steps=True)["cert_stats"].cpu().tolist()
+        certified = {"ms_per_step": round(statistics.median(mc), 4),
+                     "steps_redecided": st[0], "pairs_fp64": st[1], "picks_changed": st[2],
+                     "steps_unverified": st[3]}
 
     # end to end through the C ABI with host buffers: pinned X in, order,
     # B0, B_tau out, copies inside the events
@@ -403,7 +420,15 @@ def run_ours(args, rank, world):
     k_ms = statistics.mean(kms) if kms else None
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak = sms * SFU_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12  # T SFU slots/s at max clock
+    max_mhz = MAX_SM_MHZ
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        max_mhz = float(json.load(open(peaks_path)).get("sm_max_mhz", MAX_SM_MHZ))
+    peak = sms * SFU_NOMINAL_PER_SM_CLK * max_mhz * 1e6 / 1e12  # T SFU ops/s
+    try:
+        ex2_rate, lg2_rate = vl.sfu_rate(dev)
+    except Exception:  # diagnostic only
+        ex2_rate = lg2_rate = None
     traffic = None
     try:
         import hashlib
@@ -417,14 +442,24 @@ def run_ours(args, rank, world):
         traffic = None
     roof = None
     if k_ms:
-        ach = PS * SFU_SLOTS_PER_PAIR_SAMPLE / (k_ms * 1e-3) / 1e12
+        ach = PS * MUFU_PER_PAIR_SAMPLE / (k_ms * 1e-3) / 1e12
+        issued = PS * SFU_SLOTS_ISSUED / (k_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
-                "unit": "T SFU-slots/s", "frac": round(ach / peak, 4), "traffic": traffic,
+                "unit": "T SFU-ops/s", "frac": round(ach / peak, 4), "traffic": traffic,
                 "kernel": "pairwise_f32_kernel" if args.prec == "mixed" else "pairwise_f64_kernel",
                 "kernel_ms": round(k_ms, 4),
                 "kernel_pair_samples_per_s": PS / (k_ms * 1e-3),
-                "peak_basis": f"{sms} SMs x {SFU_PER_SM_CLK} ex2/clk x {MAX_SM_MHZ:.0f} MHz; "
-                              f"{SFU_SLOTS_PER_PAIR_SAMPLE} SFU slots per pair-sample"}
+                "count": f"{MUFU_PER_PAIR_SAMPLE} SFU operations per pair-sample (2 residuals x "
+                         f"e^-2|u|, log1p, e^-u^2/2: the method's algorithmic count)",
+                "peak_basis": f"nominal: {sms} SMs x {SFU_NOMINAL_PER_SM_CLK} ex2/clk x "
+                              f"{max_mhz:.0f} MHz (maximum SM clock)",
+                "issued": {"slots_per_pair_sample": SFU_SLOTS_ISSUED,
+                           "achieved": round(issued, 3), "frac": round(issued / peak, 4)}}
+        if ex2_rate:
+            mpeak = sms * ex2_rate * max_mhz * 1e6 / 1e12
+            roof["measured_sfu"] = {"ex2_per_clk_sm": round(ex2_rate, 2),
+                                    "lg2_per_clk_sm": round(lg2_rate, 2),
+                                    "peak": round(mpeak, 3), "frac": round(ach / mpeak, 4)}
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -438,6 +473,7 @@ def run_ours(args, rank, world):
                    "l2": "flushed by a 256 MiB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "fp64_ms_per_step": fp64_ms,
+        "certified": certified,
         "phase_ms": phases,
         "standard_search": standard,
         "e2e": {"value": job_throughput(PS, world, e2e_step), "unit": UNIT, "ms_per_step": e2e_step,
@@ -447,8 +483,8 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "clocks": clk,
     }
-    if args.batched:
-        res["batched"] = run_batched(vl, h, torch, dev, args)
+    if not args.no_batched:
+        res["batched"] = run_batched(vl, h, torch, dev, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
         try:
@@ -460,30 +496,78 @@ def run_ours(args, rank, world):
     return res
 
 
-def run_batched(vl, h, torch, dev, args):
-    """256 independent series of mixed (m, n, p) through one vl_fit_batched
-    call per step; aggregate pair-samples/s over the batch."""
+def run_batched(vl, h, torch, dev, args, stream):
+    """The 256-series mixed-size batch (m 20..400, n 250..5000, p 1..3, seeded
+    synthetic).  Mixed and certified-mixed: the phase-major batch enqueued by
+    vl_fit_batched_async, captured once into a CUDA graph after a first call
+    (which tunes the pairwise split length) and replayed; plain FP64: one
+    vl_fit_batched call.  All timed with CUDA events on the handle's stream;
+    the inputs (about 140 MB) exceed the L2 cache.  Errors: the mixed results
+    against the FP64 batch (itself within 4e-14 of the oracle in the tests)."""
     import synth
 
     insts = synth.make_batched(256, synth.config_seed(4))
-    dicts = []
-    for inst in insts:
-        o = vl.alloc_outputs(inst.m, inst.p, dev)
-        o["X"] = torch.from_numpy(inst.X).to(f"cuda:{dev}")
-        o["p"] = inst.p
-        dicts.append(o)
+    Xs = [torch.from_numpy(inst.X).to(f"cuda:{dev}") for inst in insts]
     ps = sum(pair_samples(i.m, i.n, i.p) for i in insts)
-    for _ in range(2):
-        st = vl.vl_fit_batched(h, dicts, args.prec)
-    times = []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        st = vl.vl_fit_batched(h, dicts, args.prec)  # synchronises at its end
-        times.append(time.perf_counter() - t0)
-    t = min(times)
-    return {"series": len(insts), "pair_samples": ps, "seconds": t, "value": ps / t,
-            "unit": UNIT, "failed": sum(1 for x in st if x != 0),
-            "timing": "host wall clock around the call (it synchronises), best of 3"}
+
+    def outputs():
+        ds = []
+        for inst, X in zip(insts, Xs):
+            o = vl.alloc_outputs(inst.m, inst.p, dev)
+            o["X"] = X
+            o["p"] = inst.p
+            ds.append(o)
+        return ds
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    res = {"series": len(insts), "pair_samples": ps, "unit": UNIT}
+    outs = {}
+    for prec in ("mixed", "mixed_certified"):
+        d = outputs()
+        st = torch.zeros(len(insts), dtype=torch.int32, device=f"cuda:{dev}")
+        with torch.cuda.stream(stream):
+            vl.vl_fit_batched_async(h, d, prec, st)  # tunes, sizes and uploads once
+            h.sync()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                vl.vl_fit_batched_async(h, d, prec, st)
+            g.replay()
+            torch.cuda.synchronize()
+            reps = 3 if prec == "mixed" else 2
+            ms = []
+            for _ in range(reps):
+                a, b = ev(), ev()
+                a.record(stream)
+                g.replay()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            del g
+        t = statistics.median(ms)
+        res[prec] = {"ms": round(t, 3), "value": ps / (t * 1e-3),
+                     "failed": int((st != 0).sum().item()),
+                     "timing": f"CUDA graph replay of vl_fit_batched_async, median of {reps}"}
+        outs[prec] = d
+    d64 = outputs()
+    a, b = ev(), ev()
+    a.record(h.stream)
+    st64 = vl.vl_fit_batched(h, d64, "fp64")
+    b.record(h.stream)
+    torch.cuda.synchronize()
+    t64 = a.elapsed_time(b)
+    res["fp64"] = {"ms": round(t64, 3), "value": ps / (t64 * 1e-3),
+                   "failed": sum(1 for x in st64 if x != 0),
+                   "timing": "one vl_fit_batched call (stream pool), CUDA events"}
+    for prec in ("mixed", "mixed_certified"):
+        derr = max(((o["D"] - r["D"]).abs().max() / r["D"].abs().max()).item()
+                   for o, r in zip(outs[prec], d64))
+        berr = max((o["B0"] - r["B0"]).abs().max().item() for o, r in zip(outs[prec], d64))
+        same = sum(int(torch.equal(o["order"], r["order"])) for o, r in zip(outs[prec], d64))
+        res[prec].update(max_D_err_rel=derr, max_B0_err=berr, orders_equal_fp64=same,
+                         speedup_vs_fp64=round(t64 / res[prec]["ms"], 1))
+    return res
 
 
 def run_reference(args):

@@ -59,7 +59,10 @@ typedef enum {
   VL_ERR_UNSUPPORTED = 9  /* size beyond the library's fixed limits            */
 } vl_status;
 
-typedef enum { VL_PREC_FP64 = 0, VL_PREC_MIXED = 1 } vl_precision;
+/* VL_PREC_MIXED_CERTIFIED computes like VL_PREC_MIXED and, in the calls that
+ * order (vl_fit, vl_fit_batched), decides every near tie of Eq. 3 on entries
+ * of D re-evaluated in FP64 (see vl_causal_order_certified). */
+typedef enum { VL_PREC_FP64 = 0, VL_PREC_MIXED = 1, VL_PREC_MIXED_CERTIFIED = 2 } vl_precision;
 
 /* Largest m any call accepts (the ordering kernel keeps m scores per CTA). */
 #define VL_MAX_M 4096
@@ -91,6 +94,13 @@ vl_status vl_sync(vl_handle h);
  * number of CUDA kernels this library has launched in the process. */
 vl_status vl_profile_events(vl_handle h, void* start_event, void* stop_event);
 unsigned long long vl_kernel_launches(void);
+
+/* Diagnostic, no counterpart in the paper: the measured throughput of the
+ * special-function unit on device `device`, in results per clock per SM, of
+ * ex2.approx.f32 and lg2.approx.f32 (the instructions the pairwise kernel's
+ * exponentials and logarithms use).  Synchronous; allocates two small
+ * buffers.  VL_ERR_ARG for NULL outputs. */
+vl_status vl_sfu_rate(int device, double* ex2_per_clk_sm, double* lg2_per_clk_sm);
 
 /* Human-readable text of the last error on this handle (never NULL). */
 const char* vl_last_error(vl_handle h);
@@ -134,6 +144,36 @@ vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, 
  *         |S_2nd|, 1e-300) at step k (+inf when one candidate is left).
  */
 vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, double* gap);
+
+/*
+ * Algorithm 1 over a D measured in VL_PREC_MIXED, with its near ties decided
+ * in FP64 (Algorithm 1 and Eq. 3; Eqs. 1-2 for the re-evaluated entries).
+ * The FP32 measure carries errors of about 1e-6 of max|D|, which move the
+ * scores of Eq. 3 by about 5e-5 relative; two candidates closer than that may
+ * swap.  After the search on D, every step whose picked score and some other
+ * candidate's score overlap within their error bands
+ *     band(S) = 1e-3 S + 1e-5 max|D| sqrt(S) + u (1e-5 max|D|)^2
+ * (u = variables remaining) is re-decided on exact scores: the entries D_ij
+ * of its candidates against the remaining variables are recomputed in FP64
+ * from E (standardization, rho, both standardized residuals, their entropies),
+ * the scores summed in FP64, and the argmin taken (ties: lowest index).  If a
+ * pick changes, the search resumes from that step with the corrected pick and
+ * the steps after it are checked again (up to three rounds).  The result is
+ * then the order Algorithm 1 gives on the FP64 measure wherever the FP64
+ * scores of a step differ by more than the bands.
+ * D     : m x m, as vl_pairwise_measure wrote it from E (VL_PREC_MIXED).
+ * E     : the m x n_eff data D was measured from, row stride lde >= n_eff.
+ * order : output m int32.   gap : output m doubles or NULL (as vl_causal_order,
+ *         from the FP32 scores of the final order).
+ * stats : output 4 int32 (device) or NULL: steps re-decided, pairs re-evaluated
+ *         in FP64, picks changed, steps left as the FP32 search took them
+ *         (more than 16 candidates, or after a change in the last round).
+ * Asynchronous, no host synchronisation; workspace about 12 m^2 bytes plus
+ * the ordering's.  Requires 2 <= m <= VL_MAX_M, n_eff >= 2.
+ */
+vl_status vl_causal_order_certified(vl_handle h, const double* D, const double* E, int64_t lde,
+                                    int m, int n_eff, int32_t* order, double* gap,
+                                    int32_t* stats);
 
 /*
  * Allocation-free variant of vl_causal_order (same search, same results).
@@ -235,7 +275,8 @@ typedef struct {
 
 /*
  * The whole method (steps 1-4 above) for `count` independent series of
- * possibly different (m, n, p).  The series are dealt, largest first, to a
+ * possibly different (m, n, p).  Mixed precisions run the phase-major batch
+ * of vl_fit_batched_async; VL_PREC_FP64 deals the series, largest first, to a
  * pool of up to 8 streams forked from the handle's stream and joined back
  * into it; each stream has its own workspace.  inst and inst_status are HOST
  * arrays of length count; inst_status[k] receives the instance's own status
@@ -247,6 +288,28 @@ typedef struct {
  */
 vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_precision prec,
                          vl_status* inst_status);
+
+/*
+ * The whole method for `count` series in a mixed precision (VL_PREC_MIXED or
+ * VL_PREC_MIXED_CERTIFIED), enqueued on the handle's stream without any host
+ * synchronisation (the batched form of vl_fit).  Phase-major: (A) every
+ * series' VAR fit and the measure's preparation on a pool of streams forked
+ * from the handle's stream, (B) ONE launch of the pairwise-moment kernel over
+ * a device list of (series, pair tile, sample split) work items of all
+ * series, largest first, (C) every series' finalisation of the measure,
+ * ordering and B0 / B_tau on the pool, joined back into the handle's stream.
+ * The length of the sample splits of (B) is tuned on the first call of a
+ * batch shape (every candidate timed, the fastest cached in the handle).
+ * dev_status: DEVICE array of count int32, zeroed by the call, receiving each
+ * series' device-detected status (vl_status codes).  Host-side errors of any
+ * series fail the call as a whole (nothing is launched).  After one call with
+ * the same instances, sizes and precision, a call allocates nothing, uploads
+ * nothing and can be captured into a CUDA graph; a call under capture that
+ * would need either returns VL_ERR_UNSUPPORTED.  VL_PREC_FP64 is not
+ * accepted (use vl_fit_batched).
+ */
+vl_status vl_fit_batched_async(vl_handle h, const vl_instance* inst, int count,
+                               vl_precision prec, int32_t* dev_status);
 
 #ifdef __cplusplus
 }

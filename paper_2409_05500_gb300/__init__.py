@@ -31,12 +31,15 @@ STATUS_NAMES = {
 }
 VL_PREC_FP64 = 0
 VL_PREC_MIXED = 1
-PRECISIONS = {"fp64": VL_PREC_FP64, "mixed": VL_PREC_MIXED}
+VL_PREC_MIXED_CERTIFIED = 2
+PRECISIONS = {"fp64": VL_PREC_FP64, "mixed": VL_PREC_MIXED,
+              "mixed_certified": VL_PREC_MIXED_CERTIFIED}
 
 EXPORTED = ("vl_create", "vl_destroy", "vl_set_stream", "vl_reserve", "vl_sync",
             "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_fit", "vl_var_fit",
             "vl_pairwise_measure", "vl_causal_order", "vl_causal_order_noalloc",
-            "vl_causal_order_standard", "vl_fit_b", "vl_fit_batched")
+            "vl_causal_order_certified", "vl_causal_order_standard", "vl_fit_b",
+            "vl_fit_batched", "vl_fit_batched_async", "vl_sfu_rate")
 
 
 class VLError(RuntimeError):
@@ -69,11 +72,14 @@ def _load() -> ctypes.CDLL:
         "vl_pairwise_measure": [P, P, I64, I, I, I, P, P, P],
         "vl_causal_order": [P, P, I, P, P],
         "vl_causal_order_noalloc": [P, P, I, P, P],
+        "vl_causal_order_certified": [P, P, P, I64, I, I, P, P, P],
         "vl_causal_order_standard": [P, P, I64, I, I, I, P, P],
         "vl_fit_b": [P, P, I64, I, I, P, P, I, I, P, P],
         "vl_fit_batched": [P, ctypes.POINTER(vl_instance), I, I, ctypes.POINTER(I)],
+        "vl_fit_batched_async": [P, ctypes.POINTER(vl_instance), I, I, P],
         "vl_fit": [P, P, I64, I, I, I, I, P, P, P, P, P],
         "vl_profile_events": [P, P, P],
+        "vl_sfu_rate": [I, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -91,6 +97,16 @@ _lib = _load()
 
 def lib() -> ctypes.CDLL:
     return _lib
+
+
+def sfu_rate(device: int = 0):
+    """Measured (ex2, lg2) results per clock per SM of the special-function
+    unit (diagnostic)."""
+    e, l = ctypes.c_double(), ctypes.c_double()
+    code = _lib.vl_sfu_rate(device, ctypes.byref(e), ctypes.byref(l))
+    if code != VL_OK:
+        raise VLError(code, "vl_sfu_rate failed")
+    return e.value, l.value
 
 
 def kernel_launches() -> int:
@@ -175,6 +191,19 @@ def vl_causal_order(h: Handle, D: torch.Tensor, order: torch.Tensor,
     h.check(_lib.vl_causal_order(h.h, _ptr(D), m, _ptr(order), _ptr(gap)), "vl_causal_order")
 
 
+def vl_causal_order_certified(h: Handle, D: torch.Tensor, E: torch.Tensor, order: torch.Tensor,
+                              gap: Optional[torch.Tensor] = None,
+                              stats: Optional[torch.Tensor] = None) -> None:
+    """Algorithm 1 on a mixed-precision D with near ties decided on FP64
+    entries recomputed from E (the data D was measured from).  stats: 4 int32
+    on the device (steps re-decided, pairs re-evaluated, picks changed, steps
+    left unverified) or None."""
+    m, n_eff = E.shape
+    h.check(_lib.vl_causal_order_certified(h.h, _ptr(D), _ptr(E), E.stride(0), m, n_eff,
+                                           _ptr(order), _ptr(gap), _ptr(stats)),
+            "vl_causal_order_certified")
+
+
 def vl_causal_order_noalloc(D: torch.Tensor, order: torch.Tensor,
                             gap: Optional[torch.Tensor] = None,
                             stream: Optional[torch.cuda.Stream] = None) -> None:
@@ -212,22 +241,39 @@ def vl_fit(h: Handle, X: torch.Tensor, p: int, prec: str, M: torch.Tensor, order
                         _ptr(order), _ptr(B0), _ptr(Btau), _ptr(D)), "vl_fit")
 
 
-def vl_fit_batched(h: Handle, instances: Sequence[Dict[str, torch.Tensor]], prec: str):
-    """instances: dicts with X (m x n float64 CUDA), p, and output tensors
-    order, B0, Btau, M and optionally D.  Returns the per-instance status
-    codes (0 = ok)."""
+def _instances(instances):
     arr = (vl_instance * len(instances))()
     for k, d in enumerate(instances):
         X = d["X"]
         arr[k] = vl_instance(X.data_ptr(), X.stride(0), X.shape[0], X.shape[1], int(d["p"]),
                              d["order"].data_ptr(), d["B0"].data_ptr(), d["Btau"].data_ptr(),
                              d["M"].data_ptr(), d["D"].data_ptr() if d.get("D") is not None else None)
+    return arr
+
+
+def vl_fit_batched(h: Handle, instances: Sequence[Dict[str, torch.Tensor]], prec: str):
+    """instances: dicts with X (m x n float64 CUDA), p, and output tensors
+    order, B0, Btau, M and optionally D.  Returns the per-instance status
+    codes (0 = ok)."""
+    arr = _instances(instances)
     status = (ctypes.c_int * len(instances))()
     code = _lib.vl_fit_batched(h.h, arr, len(instances), PRECISIONS[prec], status)
     out = [int(s) for s in status]
     if code != VL_OK and all(s == VL_OK for s in out):  # a failure of the call itself
         h.check(code, "vl_fit_batched")
     return out
+
+
+def vl_fit_batched_async(h: Handle, instances: Sequence[Dict[str, torch.Tensor]], prec: str,
+                         dev_status: torch.Tensor) -> None:
+    """The batch enqueued without host synchronisation (mixed precisions);
+    dev_status: int32 CUDA tensor of len(instances), filled on the device.
+    The instance array is kept on the handle object until the next call, so
+    a captured graph of this call stays valid."""
+    arr = _instances(instances)
+    h._batch_keepalive = arr
+    h.check(_lib.vl_fit_batched_async(h.h, arr, len(instances), PRECISIONS[prec],
+                                      _ptr(dev_status)), "vl_fit_batched_async")
 
 
 # ------------------------------------------------------------ conveniences
@@ -257,7 +303,11 @@ def fit(h: Handle, X: torch.Tensor, p: int, prec: str = "mixed", steps: bool = F
                gap=torch.empty((m,), **f64))
     vl_var_fit(h, X, p, prec, out["M"], E)
     vl_pairwise_measure(h, E, prec, out["Hx"], out["Hr"], out["D"])
-    vl_causal_order(h, out["D"], out["order"], out["gap"])
+    if prec == "mixed_certified":
+        out["cert_stats"] = torch.zeros(4, dtype=torch.int32, device=X.device)
+        vl_causal_order_certified(h, out["D"], E, out["order"], out["gap"], out["cert_stats"])
+    else:
+        vl_causal_order(h, out["D"], out["order"], out["gap"])
     vl_fit_b(h, E, out["order"], out["M"], prec, out["B0"], out["Btau"])
     h.sync()
     return out

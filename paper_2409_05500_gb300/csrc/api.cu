@@ -132,14 +132,30 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   const int n_eff = n - p, mp = m * p, q = m * (p + 1);
   const int64_t ldc = round_up(n, 4);
   const int nblk = (mp + CHOL_NB - 1) / CHOL_NB;
-  const size_t part_cap = (size_t)16 * std::max((size_t)m * m, (size_t)mp * mp);
+  const size_t part_cap =
+      (size_t)16 * std::max((size_t)m * m, (size_t)mp * mp) +
+      (sizeof(T) == 4 ? (size_t)4 * m * (p + 1) * m * (p + 1) : 0);  // tensor-core split-K
+  const bool tc = sizeof(T) == 4;  // mixed: the Gram on the tensor cores
+  const int64_t kp = tg_kpad(n_eff), plane = (int64_t)q * kp;
   T *Xc, *Gzz, *Gzy, *dinv;
   double *mu, *wbar, *G, *cst, *Ew, *part, *diag0;
+  char* S = nullptr;
+  int* exps = nullptr;
+  float *nhi = nullptr, *nlo = nullptr, *rr = nullptr;
   vl_status s = with_workspace(x, [&](Arena& a) {
     Xc = a.take<T>((size_t)m * ldc);
     mu = a.take<double>(m);
     wbar = a.take<double>((size_t)(p + 1) * m);
-    G = a.take<double>((size_t)mp * q);
+    if (tc) {
+      G = a.take<double>((size_t)q * q) + (size_t)m * q;  // rows m.. of the full W W^T
+      S = a.take<char>(3 * (size_t)plane * 2);
+      exps = a.take<int>(q);
+      nhi = a.take<float>((size_t)mp * q);
+      nlo = a.take<float>((size_t)mp * q);
+      rr = a.take<float>((size_t)mp * m);
+    } else {
+      G = a.take<double>((size_t)mp * q);
+    }
     Gzz = a.take<T>((size_t)mp * mp);
     Gzy = a.take<T>((size_t)mp * m);
     dinv = a.take<T>((size_t)nblk * CHOL_NB * CHOL_NB);
@@ -153,18 +169,35 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   Ctx cx = make_ctx(x, part, part_cap);
   cudaStream_t st = x.s;
   launch_var_prep<T>(X, ldx, m, n, p, Xc, ldc, mu, wbar, x.st, st);
-  // lagged Gram: rows of Z (lags 1..p) against rows of W = [Y; Z]
-  for (int t1 = 1; t1 <= p; ++t1)
-    for (int b2 = 0; b2 <= p; ++b2) {
-      View<T> A{Xc + (p - t1), ldc, 1};
-      View<T> B{Xc + (p - b2), ldc, 1};
-      launch_gemm<T, double>(cx, m, m, n_eff, 1.0, A, B, 0.0,
-                             G + (int64_t)(t1 - 1) * m * q + (int64_t)b2 * m, q, false);
-    }
-  launch_var_normal_eq<T>(G, m, p, n_eff, wbar, Gzz, Gzy, st);
+  if constexpr (sizeof(T) == 4) {
+    // W W^T on the tensor cores: the lag windows sliced once, the symmetric
+    // q x q product; its rows m.. (the Z rows) are G
+    launch_slice_lags(Xc, ldc, m, n, p, kp, S, plane, exps, st);
+    if (!launch_tcgram_sym(cx, S, q, (int)kp, kp, plane, exps, G - (size_t)m * q, q))
+      return fail(x.h, VL_ERR_CUDA, "vl_var_fit: tensor map encoding unavailable");
+  } else {
+    // lagged Gram: rows of Z (lags 1..p) against rows of W = [Y; Z]
+    for (int t1 = 1; t1 <= p; ++t1)
+      for (int b2 = 0; b2 <= p; ++b2) {
+        View<T> A{Xc + (p - t1), ldc, 1};
+        View<T> B{Xc + (p - b2), ldc, 1};
+        launch_gemm<T, double>(cx, m, m, n_eff, 1.0, A, B, 0.0,
+                               G + (int64_t)(t1 - 1) * m * q + (int64_t)b2 * m, q, false);
+      }
+  }
+  launch_var_normal_eq<T>(G, m, p, n_eff, wbar, Gzz, Gzy, st, nhi, nlo);
   chol_blocked<T>(cx, Gzz, mp, mp, dinv, diag0);
   chol_solve_blocked<T>(cx, Gzz, mp, dinv, mp, Gzy, m, m, true);
-  launch_var_coef<T>(Gzy, m, p, wbar, M, cst, st);
+  if constexpr (sizeof(T) == 4) {
+    // one step of iterative refinement: r = G_zy - G_zz beta0 in
+    // double-float, the correction from the same FP32 factor
+    launch_refine_residual(nhi, nlo, m, p, Gzy, rr, st);
+    chol_solve_blocked<T>(cx, Gzz, mp, dinv, mp, rr, m, m, true);
+    launch_refine_apply(Gzy, rr, m, p, M, st);
+    launch_var_cst<T>(Gzy, m, p, wbar, cst, st);
+  } else {
+    launch_var_coef<T>(Gzy, m, p, wbar, M, cst, st);
+  }
   launch_var_resid_init(X, ldx, m, n, p, mu, cst, E, n_eff, st);
   for (int tau = 1; tau <= p; ++tau) {
     View<T> A{Gzy + (int64_t)(tau - 1) * m * m, 1, m};  // A(i, k) = M_tau[i][k]
@@ -182,30 +215,35 @@ struct CovOut {
   double* hx;  // 2m moments of the standardized variables
 };
 
+// Statistics of the standardization and the centred cross products C of E.
+// Mixed precision: C on the tensor cores from exact bf16 slices
+// (k_tcgram.cu); FP64: the FP64 GEMM.
 template <class T>
-void cov_and_stats(const Ctx& cx, const double* E, int64_t lde, int m, int n, const CovOut& o,
-                   void* scratch) {
+vl_status cov_and_stats(const Ctx& cx, const double* E, int64_t lde, int m, int n,
+                        const CovOut& o, void* scratch) {
   cudaStream_t st = cx.s;
   launch_standardize<T>(E, lde, m, n, o.mu, o.isd, o.hx, cx.st, st);
-  const int64_t ldc = round_up(n, 4);
   if constexpr (sizeof(T) == 4) {
-    float* hi = static_cast<float*>(scratch);
-    float* lo = hi + (size_t)m * ldc;
-    launch_split_center(E, lde, m, n, o.mu, hi, lo, ldc, st);
-    View<float> Vh{hi, ldc, 1}, Vl{lo, ldc, 1};
-    launch_gemm_split(cx, m, m, n, Vh, Vl, Vh, Vl, o.C, m, true);
+    const int64_t kp = tg_kpad(n), plane = (int64_t)m * kp;
+    char* S = static_cast<char*>(scratch);
+    int* exps = reinterpret_cast<int*>(S + round_up(3 * plane * 2, 256));
+    launch_slice_center(E, lde, o.mu, m, n, kp, S, plane, exps, st);
+    if (!launch_tcgram_sym(cx, S, m, (int)kp, kp, plane, exps, o.C, m)) return VL_ERR_CUDA;
   } else {
+    const int64_t ldc = round_up(n, 4);
     double* ec = static_cast<double*>(scratch);
     launch_center64(E, lde, m, n, o.mu, ec, ldc, st);
     View<double> V{ec, ldc, 1};
     launch_gemm<double, double>(cx, m, m, n, 1.0, V, V, 0.0, o.C, m, false);
   }
+  return VL_OK;
 }
 
 template <class T>
 size_t cov_scratch_bytes(int m, int n) {
-  const int64_t ldc = round_up(n, 4);
-  return sizeof(T) == 4 ? 2 * sizeof(float) * (size_t)m * ldc : sizeof(double) * (size_t)m * ldc;
+  if (sizeof(T) == 4)
+    return (size_t)round_up(3 * (int64_t)m * tg_kpad(n) * 2, 256) + sizeof(int) * (size_t)m;
+  return sizeof(double) * (size_t)m * round_up(n, 4);
 }
 
 template <class T>
@@ -250,7 +288,8 @@ vl_status pairwise_impl(Exec& x, const double* E, int64_t lde, int m, int n, dou
   vl_handle h = x.h;
   Ctx cx = make_ctx(x, gpart, part_cap);
   cudaStream_t st = x.s;
-  cov_and_stats<T>(cx, E, lde, m, n, o, scratch);
+  if (cov_and_stats<T>(cx, E, lde, m, n, o, scratch) != VL_OK)
+    return fail(h, VL_ERR_CUDA, "vl_pairwise_measure: tensor map encoding unavailable");
   launch_pair_consts(o.C, m, rho32, c32, rho64, x.st, st);
   launch_transpose_std<T>(E, lde, m, n, o.mu, o.isd, xt, pl.m_pad, pl.n_pad, st);
   if (h->prof_start) cudaEventRecord(h->prof_start, st);
@@ -298,7 +337,8 @@ vl_status fit_b_impl(Exec& x, const double* E, int64_t lde, int m, int n,
   cudaStream_t st = x.s;
   const double* C = C_in;
   if (!C) {
-    cov_and_stats<T>(cx, E, lde, m, n, o, scratch);
+    if (cov_and_stats<T>(cx, E, lde, m, n, o, scratch) != VL_OK)
+      return fail(x.h, VL_ERR_CUDA, "vl_fit_b: tensor map encoding unavailable");
     C = o.C;
   }
   launch_permute_cov<T>(C, m, 1.0 / n, order, Sp, m, st);
@@ -335,6 +375,22 @@ vl_status order_impl(Exec& x, const double* D, int m, int32_t* order, double* ga
   if (s != VL_OK || x.measure) return s;
   launch_causal_order(D, m, ows, order, gap, x.st, x.s);
   return check_launch(x.h, "vl_causal_order");
+}
+
+// Algorithm 1 on an FP32-measure D with its near ties re-decided in FP64
+// from E (k_certify.cu).
+vl_status order_certified_impl(Exec& x, const double* D, const double* E, int64_t lde, int m,
+                               int n, int32_t* order, double* gap, int32_t* stats) {
+  char *ows, *cws;
+  vl_status s = with_workspace(x, [&](Arena& a) {
+    ows = a.take<char>(order_ws_bytes(m));
+    cws = a.take<char>(certify_ws_bytes(m));
+  });
+  if (s != VL_OK || x.measure) return s;
+  launch_causal_order(D, m, ows, order, nullptr, x.st, x.s, nullptr, certify_spick(cws, m));
+  launch_certify(D, E, lde, m, n, ows, cws, order, stats, x.h->num_sms, x.s);
+  if (gap) launch_order_gaps(ows, m, order, gap, x.s);
+  return check_launch(x.h, "vl_causal_order_certified");
 }
 
 // The iterative search of Sec. 3: m - 1 iterations of (pairwise measure of
@@ -399,18 +455,22 @@ vl_status order_standard_impl(Exec& x, const double* E, int64_t lde, int m, int 
 // The whole method on one series, on one execution context.  E, C and D are
 // per-series buffers of the caller (E: m x (n-p), C, D: m x m).
 template <class T>
-vl_status fit_one(Exec& x, const vl_instance& I, double* E, double* C, double* D) {
+vl_status fit_one(Exec& x, const vl_instance& I, double* E, double* C, double* D,
+                  bool certified = false) {
   const int m = I.m, n_eff = I.n - I.p;
   vl_status s = var_fit_impl<T>(x, I.X, I.ldx, m, I.n, I.p, I.M, E);
   if (s == VL_OK) s = pairwise_impl<T>(x, E, n_eff, m, n_eff, nullptr, nullptr, D, C);
-  if (s == VL_OK) s = order_impl(x, D, m, I.order, nullptr);
+  if (s == VL_OK)
+    s = certified ? order_certified_impl(x, D, E, n_eff, m, n_eff, I.order, nullptr, nullptr)
+                  : order_impl(x, D, m, I.order, nullptr);
   if (s == VL_OK) s = fit_b_impl<T>(x, E, n_eff, m, n_eff, I.order, I.M, I.p, I.B0, I.Btau, C);
   return s;
 }
 
 vl_status validate_prec(vl_handle h, vl_precision prec) {
-  if (prec != VL_PREC_FP64 && prec != VL_PREC_MIXED)
-    return fail(h, VL_ERR_ARG, "precision must be VL_PREC_FP64 or VL_PREC_MIXED");
+  if (prec != VL_PREC_FP64 && prec != VL_PREC_MIXED && prec != VL_PREC_MIXED_CERTIFIED)
+    return fail(h, VL_ERR_ARG,
+                "precision must be VL_PREC_FP64, VL_PREC_MIXED or VL_PREC_MIXED_CERTIFIED");
   return VL_OK;
 }
 
@@ -422,6 +482,307 @@ vl_status check_instance(vl_handle h, const vl_instance& I) {
   if ((int64_t)I.n - I.p <= (int64_t)I.m * I.p + 1)
     return fail(h, VL_ERR_RANK, "vl_fit_batched: n - p <= m p + 1");
   return VL_OK;
+}
+
+// ------------------------------------------------ phase-major mixed batches
+// A mixed-precision batch runs in three phases: (A) every instance's VAR fit
+// and the measure's preparation (statistics, tensor-core covariance, pair
+// constants, time-major standardized data) on a pool of streams; (B) ONE
+// launch of the pairwise kernel over a device list of (instance, pair tile,
+// sample split) work items of all instances, largest first; (C) every
+// instance's finalisation of the measure, ordering and B0 / B_tau on the
+// pool.  The per-instance buffers live in one handle-owned allocation; the
+// work list is uploaded once per batch layout, so after a first call the
+// whole batch can be captured into one CUDA graph (vl_fit_batched_async).
+// The length of the sample splits of phase B is chosen by an autotuner: on
+// the first uncaptured call of a batch shape every candidate length is timed
+// (CUDA events) and the fastest is cached in the handle.
+
+struct InstBufs {
+  PairPlan pl;  // the plan phase B and the finalisation use
+  double *E, *C, *D, *mu, *isd, *hx;
+  float *rho32, *c32, *xt, *parts;
+};
+
+constexpr int SPLIT_CANDIDATES[] = {256, 512, 1024, 2048, 4096};
+constexpr int SPLIT_MIN = 256;      // buffers hold the partials of the shortest split
+constexpr int SPLIT_DEFAULT = 1024;  // used under capture before any tuning
+
+void carve_inst(Arena& a, const vl_instance& I, InstBufs& b) {
+  const size_t m = I.m, ne = I.n - I.p;
+  const PairPlan big = plan_pairwise_split(I.m, I.n - I.p, SPLIT_MIN);
+  b.E = a.take<double>(m * ne);
+  b.C = a.take<double>(m * m);
+  b.D = a.take<double>(m * m);
+  b.mu = a.take<double>(m);
+  b.isd = a.take<double>(m);
+  b.hx = a.take<double>(2 * m);
+  b.rho32 = a.take<float>(m * m);
+  b.c32 = a.take<float>(m * m);
+  b.xt = a.take<float>((size_t)big.n_pad * big.m_pad);
+  b.parts = a.take<float>((size_t)big.splits * 4 * m * m);
+}
+
+// Phase A of one instance.
+vl_status batch_prep(Exec& x, const vl_instance& I, InstBufs& b) {
+  const int m = I.m, n_eff = I.n - I.p;
+  vl_status s = var_fit_impl<float>(x, I.X, I.ldx, m, I.n, I.p, I.M, b.E);
+  if (s != VL_OK) return s;
+  const size_t part_cap =
+      std::max((size_t)16 * m * m, std::min((size_t)64 * m * m, (size_t)1 << 20));
+  void* scratch;
+  double* gpart;
+  s = with_workspace(x, [&](Arena& a) {
+    scratch = a.take<char>(cov_scratch_bytes<float>(m, n_eff));
+    gpart = a.take<double>(part_cap);
+  });
+  if (s != VL_OK || x.measure) return s;
+  Ctx cx = make_ctx(x, gpart, part_cap);
+  CovOut o{b.C, b.mu, b.isd, b.hx};
+  if (cov_and_stats<float>(cx, b.E, n_eff, m, n_eff, o, scratch) != VL_OK)
+    return fail(x.h, VL_ERR_CUDA, "vl_fit_batched: tensor map encoding unavailable");
+  launch_pair_consts(b.C, m, b.rho32, b.c32, nullptr, x.st, x.s);
+  launch_transpose_std<float>(b.E, n_eff, m, n_eff, b.mu, b.isd, b.xt, b.pl.m_pad, b.pl.n_pad,
+                              x.s);
+  return VL_OK;
+}
+
+// Phase C of one instance.
+vl_status batch_finish(Exec& x, const vl_instance& I, const InstBufs& b, bool certified) {
+  const int m = I.m, n_eff = I.n - I.p;
+  double* Hr;
+  vl_status s = with_workspace(x, [&](Arena& a) { Hr = a.take<double>((size_t)m * m); });
+  if (s != VL_OK) return s;
+  double* D = I.D ? I.D : b.D;
+  if (!x.measure) launch_measure_finalize(b.parts, b.pl, b.hx, nullptr, Hr, D, true, x.s);
+  s = certified ? order_certified_impl(x, D, b.E, n_eff, m, n_eff, I.order, nullptr, nullptr)
+                : order_impl(x, D, m, I.order, nullptr);
+  if (s == VL_OK) s = fit_b_impl<float>(x, b.E, n_eff, m, n_eff, I.order, I.M, I.p, I.B0, I.Btau,
+                                        b.C);
+  return s;
+}
+
+unsigned long long mix64(unsigned long long h, unsigned long long v) {
+  h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+// The work items of phase B for split length `len`, largest first; the plans
+// of the instances are set to that length.
+void build_items(const vl_instance* inst, const std::vector<int>& idx, std::vector<InstBufs>& B,
+                 int len, std::vector<PairJob>& jobs, std::vector<int4>& items) {
+  jobs.clear();
+  items.clear();
+  std::vector<std::pair<double, int4>> w;
+  for (size_t j = 0; j < idx.size(); ++j) {
+    const vl_instance& I = inst[idx[j]];
+    InstBufs& b = B[j];
+    b.pl = plan_pairwise_split(I.m, I.n - I.p, len);
+    jobs.push_back(make_pair_job(b.xt, b.pl, b.rho32, b.c32, b.parts));
+    const int T = b.pl.m_pad / 32;
+    for (int t = 0, q = 0; t < T; ++t)
+      for (int u = t; u < T; ++u, ++q) {
+        // pairs with i < j < m in tile (t, u)
+        const int i0 = 32 * t, j0 = 32 * u;
+        double pairs = 0;
+        for (int i = i0; i < std::min(i0 + 32, I.m); ++i)
+          pairs += std::max(0, std::min(j0 + 32, I.m) - std::max(j0, i + 1));
+        for (int z = 0; z < b.pl.splits; ++z) {
+          const int n_run = ((I.n - I.p + 15) / 16) * 16;
+          const int len_z = std::min(b.pl.t_per_split, n_run - z * b.pl.t_per_split);
+          w.push_back({pairs * std::max(len_z, 0) + 1e-3, make_int4((int)j, q, z, 0)});
+        }
+      }
+  }
+  std::stable_sort(w.begin(), w.end(),
+                   [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+                     return a.first > b.first;
+                   });
+  for (auto& e : w) items.push_back(e.second);
+}
+
+// The phase-major batch over the valid instances idx (already checked on the
+// host).  dstat: per-instance device status words (count of the caller's
+// array, indexed by instance).  Allocates only if a buffer must grow, uploads
+// the work list only when the batch layout changed, and tunes the split
+// length only outside stream capture.
+vl_status batched_mixed(vl_handle h, const vl_instance* inst, const std::vector<int>& idx,
+                        bool certified, int* dstat) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(h->stream, &cap);
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  const int S = (int)std::min<size_t>(idx.size(), (size_t)BATCH_STREAMS);
+  if (S == 0) return VL_OK;
+  // per-instance buffers, one allocation
+  std::vector<InstBufs> B(idx.size());
+  Arena sz;
+  for (size_t j = 0; j < idx.size(); ++j) carve_inst(sz, inst[idx[j]], B[j]);
+  if (sz.off + 512 > h->bbuf_cap && capturing)
+    return fail(h, VL_ERR_UNSUPPORTED, "vl_fit_batched_async: call once outside capture first");
+  vl_status s = grow(h, &h->bbuf, &h->bbuf_cap, sz.off + 512, h->stream);
+  if (s != VL_OK) return s;
+  Arena ar;
+  ar.base = static_cast<char*>(h->bbuf);
+  ar.cap = h->bbuf_cap;
+  for (size_t j = 0; j < idx.size(); ++j) {
+    carve_inst(ar, inst[idx[j]], B[j]);
+    B[j].pl = plan_pairwise_split(inst[idx[j]].m, inst[idx[j]].n - inst[idx[j]].p, SPLIT_DEFAULT);
+  }
+  // per-stream workspace: the largest need of phases A and C
+  size_t ws_need = 0;
+  for (size_t j = 0; j < idx.size(); ++j) {
+    Exec probe{h, nullptr, nullptr, nullptr, nullptr, true, 0};
+    batch_prep(probe, inst[idx[j]], B[j]);
+    batch_finish(probe, inst[idx[j]], B[j], certified);
+    ws_need = std::max(ws_need, probe.need);
+  }
+  if ((int)h->pool.size() < S) h->pool.resize(S);
+  for (int q = 0; q < S; ++q) {
+    PoolSlot& ps = h->pool[q];
+    if ((!ps.stream || !ps.done || ps.ws_cap < ws_need) && capturing)
+      return fail(h, VL_ERR_UNSUPPORTED, "vl_fit_batched_async: call once outside capture first");
+    if (!ps.stream && cudaStreamCreateWithFlags(&ps.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, VL_ERR_CUDA, "vl_fit_batched: stream creation failed");
+    }
+    if (!ps.done && cudaEventCreateWithFlags(&ps.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, VL_ERR_CUDA, "vl_fit_batched: event creation failed");
+    }
+    s = grow(h, &ps.ws, &ps.ws_cap, ws_need, ps.stream);
+    if (s != VL_OK) return s;
+  }
+  // split length: tuned once per batch shape
+  unsigned long long shape = mix64(0, idx.size());
+  for (int k : idx) shape = mix64(mix64(mix64(shape, inst[k].m), inst[k].n), inst[k].p);
+  auto tuned = h->split_tune.find(shape);
+  const bool tune = tuned == h->split_tune.end() && !capturing;
+  int len = tuned != h->split_tune.end() ? tuned->second : SPLIT_DEFAULT;
+  std::vector<PairJob> jobs;
+  std::vector<int4> items;
+  // upload the work list of `len` if the layout differs from the device copy
+  auto upload = [&](int L) -> vl_status {
+    build_items(inst, idx, B, L, jobs, items);
+    const unsigned long long sig =
+        mix64(mix64(mix64(shape, (unsigned long long)(uintptr_t)h->bbuf), L), items.size());
+    if (sig == h->blist_sig) return VL_OK;
+    if (capturing)
+      return fail(h, VL_ERR_UNSUPPORTED, "vl_fit_batched_async: call once outside capture first");
+    const size_t bytes = jobs.size() * sizeof(PairJob) + 256 + items.size() * sizeof(int4);
+    vl_status r = grow(h, &h->blist, &h->blist_cap, bytes, h->stream);
+    if (r != VL_OK) return r;
+    char* d = static_cast<char*>(h->blist);
+    const size_t joff = ((jobs.size() * sizeof(PairJob)) + 255) & ~size_t(255);
+    if (cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(PairJob), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d + joff, items.data(), items.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, VL_ERR_CUDA, "vl_fit_batched: work list upload failed");
+    }
+    h->blist_sig = sig;
+    h->blist_items = (int)items.size();
+    return VL_OK;
+  };
+  auto list_ptrs = [&](const PairJob*& J, const int4*& It) {
+    char* d = static_cast<char*>(h->blist);
+    J = reinterpret_cast<const PairJob*>(d);
+    It = reinterpret_cast<const int4*>(
+        d + (((jobs.size() * sizeof(PairJob)) + 255) & ~size_t(255)));
+  };
+  if (!tune) {
+    s = upload(len);
+    if (s != VL_OK) return s;
+  }
+  // fork: every pool stream waits for the handle stream
+  auto fork = [&]() {
+    cudaEventRecord(h->pool[0].done, h->stream);
+    for (int q = 0; q < S; ++q) cudaStreamWaitEvent(h->pool[q].stream, h->pool[0].done, 0);
+  };
+  auto join = [&]() {
+    for (int q = 0; q < S; ++q) {
+      cudaEventRecord(h->pool[q].done, h->pool[q].stream);
+      cudaStreamWaitEvent(h->stream, h->pool[q].done, 0);
+    }
+  };
+  // phase A, instances largest first (idx is sorted so), dealt round robin
+  fork();
+  for (size_t j = 0; j < idx.size(); ++j) {
+    PoolSlot& ps = h->pool[j % S];
+    Exec x{h, ps.stream, dstat + idx[j], &ps.ws, &ps.ws_cap, false, 0};
+    s = batch_prep(x, inst[idx[j]], B[j]);
+    if (s != VL_OK) break;
+  }
+  join();
+  if (s != VL_OK) return s;
+  // phase B
+  const int grid = h->num_sms;  // one CTA per SM (the kernel's occupancy)
+  const PairJob* J;
+  const int4* It;
+  if (tune) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int L : SPLIT_CANDIDATES) {
+      s = upload(L);
+      if (s != VL_OK) break;
+      list_ptrs(J, It);
+      cudaEventRecord(e0, h->stream);
+      launch_pairwise_f32_list(J, It, (int)items.size(), grid, h->stream);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        len = L;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != VL_OK) return s;
+    h->split_tune[shape] = len;
+    s = upload(len);
+    if (s != VL_OK) return s;
+  }
+  build_items(inst, idx, B, len, jobs, items);  // the plans of the chosen length
+  list_ptrs(J, It);
+  launch_pairwise_f32_list(J, It, h->blist_items, grid, h->stream);
+  // phase C
+  fork();
+  for (size_t j = 0; j < idx.size(); ++j) {
+    PoolSlot& ps = h->pool[j % S];
+    Exec x{h, ps.stream, dstat + idx[j], &ps.ws, &ps.ws_cap, false, 0};
+    s = batch_finish(x, inst[idx[j]], B[j], certified);
+    if (s != VL_OK) break;
+  }
+  join();
+  if (s != VL_OK) return s;
+  return check_launch(h, "vl_fit_batched");
+}
+
+
+// Wait for the batch and merge the per-instance device statuses into the
+// host statuses; returns the first non-OK status.
+vl_status read_batch_status(vl_handle h, const std::vector<int>& idx, int count,
+                            vl_status* inst_status) {
+  std::vector<int> dev(count, 0);
+  cudaError_t e = cudaMemcpyAsync(dev.data(), h->bstatus, sizeof(int) * count,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    for (int k : idx) inst_status[k] = VL_ERR_CUDA;
+    return fail(h, VL_ERR_CUDA, std::string("vl_fit_batched: ") + cudaGetErrorString(e));
+  }
+  for (int k : idx)
+    if (inst_status[k] == VL_OK && dev[k] != 0) inst_status[k] = (vl_status)dev[k];
+  vl_status err = VL_OK;
+  for (int k = 0; k < count; ++k)
+    if (err == VL_OK && inst_status[k] != VL_OK) err = inst_status[k];
+  if (err != VL_OK && h->last_error.empty()) h->last_error = "vl_fit_batched: an instance failed";
+  return err;
 }
 
 // A batch: instances are dealt, largest first, to a pool of streams forked
@@ -449,8 +810,8 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
       const vl_instance& I = inst[k];
       Exec probe{h, nullptr, nullptr, nullptr, nullptr, true, 0};
       double* dummy = nullptr;
-      if (prec == VL_PREC_MIXED)
-        fit_one<float>(probe, I, dummy, dummy, dummy);
+      if (prec != VL_PREC_FP64)
+        fit_one<float>(probe, I, dummy, dummy, dummy, prec == VL_PREC_MIXED_CERTIFIED);
       else
         fit_one<double>(probe, I, dummy, dummy, dummy);
       ws_need = std::max(ws_need, probe.need);
@@ -472,6 +833,15 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
         return fail(h, VL_ERR_NOMEM, "vl_fit_batched: status array allocation failed");
       }
       h->bstatus_cap = count;
+    }
+    if (prec != VL_PREC_FP64) {  // mixed precisions: the phase-major batch
+      cudaMemsetAsync(h->bstatus, 0, sizeof(int) * count, h->stream);
+      s = batched_mixed(h, inst, idx, prec == VL_PREC_MIXED_CERTIFIED, h->bstatus);
+      if (s != VL_OK) {
+        for (int k : idx) inst_status[k] = s;
+        return s;
+      }
+      return read_batch_status(h, idx, count, inst_status);
     }
     for (int q = 0; q < S && s == VL_OK; ++q) {
       PoolSlot& ps = h->pool[q];
@@ -505,7 +875,7 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
       double* E = static_cast<double*>(ps.buf);
       double* C = E + (size_t)I.m * (I.n - I.p);
       double* D = I.D ? I.D : C + (size_t)I.m * I.m;
-      vl_status r = prec == VL_PREC_MIXED ? fit_one<float>(x, I, E, C, D)
+      vl_status r = prec != VL_PREC_FP64 ? fit_one<float>(x, I, E, C, D, prec == VL_PREC_MIXED_CERTIFIED)
                                           : fit_one<double>(x, I, E, C, D);
       if (r != VL_OK) inst_status[k] = r;
     }
@@ -514,16 +884,7 @@ vl_status batched_impl(vl_handle h, const vl_instance* inst, int count, vl_preci
       cudaEventRecord(h->pool[q].done, h->pool[q].stream);
       cudaStreamWaitEvent(h->stream, h->pool[q].done, 0);
     }
-    std::vector<int> dev(count, 0);
-    cudaError_t e = cudaMemcpyAsync(dev.data(), h->bstatus, sizeof(int) * count,
-                                    cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-      for (int k : idx) inst_status[k] = VL_ERR_CUDA;
-      return fail(h, VL_ERR_CUDA, std::string("vl_fit_batched: ") + cudaGetErrorString(e));
-    }
-    for (int k : idx)
-      if (inst_status[k] == VL_OK && dev[k] != 0) inst_status[k] = (vl_status)dev[k];
+    return read_batch_status(h, idx, count, inst_status);
   }
   for (int k = 0; k < count; ++k)
     if (err == VL_OK && inst_status[k] != VL_OK) err = inst_status[k];
@@ -580,6 +941,8 @@ vl_status vl_destroy(vl_handle h) {
     }
     if (h->bstatus) cudaFree(h->bstatus);
     if (h->sbuf) cudaFree(h->sbuf);
+    if (h->bbuf) cudaFree(h->bbuf);
+    if (h->blist) cudaFree(h->blist);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
   }
@@ -606,6 +969,10 @@ vl_status vl_reserve(vl_handle h, int m, int n, int p) {
   // pairwise partials of a problem too small to fill one wave: shorter
   // splits, at most one CTA per SM, 4096 doubles per CTA beyond the m^2 terms
   b += 8 * (size_t)4096 * h->num_sms;
+  // mixed path: the tensor-core Grams (full W W^T, its split-K partials, the
+  // bf16 slices of W and of E) and the certified ordering's FP64 cache
+  const size_t q = (size_t)m * (std::max(p, 1) + 1);
+  b += 8 * 5 * q * q + 6 * (q + (size_t)m) * ln + 24 * mm;
   DeviceGuard g(h->device);
   return ensure_ws(h, b);
 }
@@ -656,7 +1023,7 @@ vl_status vl_var_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, in
     return fail(h, VL_ERR_RANK, "vl_var_fit: n - p <= m p + 1, the VAR has no unique fit");
   DeviceGuard g(h->device);
   Exec x = handle_exec(h);
-  return prec == VL_PREC_MIXED ? var_fit_impl<float>(x, X, ldx, m, n, p, M, E)
+  return prec != VL_PREC_FP64 ? var_fit_impl<float>(x, X, ldx, m, n, p, M, E)
                                : var_fit_impl<double>(x, X, ldx, m, n, p, M, E);
 }
 
@@ -670,7 +1037,7 @@ vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, 
     return fail(h, VL_ERR_SHAPE, "vl_pairwise_measure: need 2 <= m <= VL_MAX_M, n_eff >= 2, lde >= n_eff");
   DeviceGuard g(h->device);
   Exec x = handle_exec(h);
-  return prec == VL_PREC_MIXED ? pairwise_impl<float>(x, E, lde, m, n_eff, Hx, Hr, D, nullptr)
+  return prec != VL_PREC_FP64 ? pairwise_impl<float>(x, E, lde, m, n_eff, Hx, Hr, D, nullptr)
                                : pairwise_impl<double>(x, E, lde, m, n_eff, Hx, Hr, D, nullptr);
 }
 
@@ -681,6 +1048,20 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
   DeviceGuard g(h->device);
   Exec x = handle_exec(h);
   return order_impl(x, D, m, order, gap);
+}
+
+vl_status vl_causal_order_certified(vl_handle h, const double* D, const double* E, int64_t lde,
+                                    int m, int n_eff, int32_t* order, double* gap,
+                                    int32_t* stats) {
+  if (!h) return VL_ERR_ARG;
+  if (!D || !E || !order)
+    return fail(h, VL_ERR_ARG, "vl_causal_order_certified: D, E and order must not be NULL");
+  if (m < 2 || n_eff < 2 || m > VL_MAX_M || lde < n_eff)
+    return fail(h, VL_ERR_SHAPE,
+                "vl_causal_order_certified: need 2 <= m <= VL_MAX_M, n_eff >= 2, lde >= n_eff");
+  DeviceGuard g(h->device);
+  Exec x = handle_exec(h);
+  return order_certified_impl(x, D, E, lde, m, n_eff, order, gap, stats);
 }
 
 vl_status vl_causal_order_standard(vl_handle h, const double* E, int64_t lde, int m, int n_eff,
@@ -694,7 +1075,7 @@ vl_status vl_causal_order_standard(vl_handle h, const double* E, int64_t lde, in
                 "vl_causal_order_standard: need 2 <= m <= VL_MAX_M, n_eff >= 2, lde >= n_eff");
   DeviceGuard g(h->device);
   Exec x = handle_exec(h);
-  return prec == VL_PREC_MIXED ? order_standard_impl<float>(x, E, lde, m, n_eff, order, gap)
+  return prec != VL_PREC_FP64 ? order_standard_impl<float>(x, E, lde, m, n_eff, order, gap)
                                : order_standard_impl<double>(x, E, lde, m, n_eff, order, gap);
 }
 
@@ -730,7 +1111,31 @@ vl_status vl_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, int p,
   double* C = E + m * ne;
   if (!D) D = C + mm;
   Exec x = handle_exec(h);
-  return prec == VL_PREC_MIXED ? fit_one<float>(x, I, E, C, D) : fit_one<double>(x, I, E, C, D);
+  return prec != VL_PREC_FP64 ? fit_one<float>(x, I, E, C, D, prec == VL_PREC_MIXED_CERTIFIED)
+                               : fit_one<double>(x, I, E, C, D);
+}
+
+vl_status vl_fit_batched_async(vl_handle h, const vl_instance* inst, int count,
+                               vl_precision prec, int32_t* dev_status) {
+  if (!h) return VL_ERR_ARG;
+  if (count < 0 || (count > 0 && (!inst || !dev_status)))
+    return fail(h, VL_ERR_ARG, "vl_fit_batched_async: inst and dev_status must not be NULL");
+  if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
+  if (prec == VL_PREC_FP64)
+    return fail(h, VL_ERR_UNSUPPORTED, "vl_fit_batched_async: mixed precisions only");
+  if (count == 0) return VL_OK;
+  std::vector<int> idx;
+  for (int k = 0; k < count; ++k) {
+    const vl_status s = check_instance(h, inst[k]);
+    if (s != VL_OK) return s;
+    idx.push_back(k);
+  }
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return (double)inst[a].m * inst[a].m * inst[a].n > (double)inst[b].m * inst[b].m * inst[b].n;
+  });
+  DeviceGuard g(h->device);
+  cudaMemsetAsync(dev_status, 0, sizeof(int32_t) * count, h->stream);
+  return batched_mixed(h, inst, idx, prec == VL_PREC_MIXED_CERTIFIED, dev_status);
 }
 
 vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_precision prec,

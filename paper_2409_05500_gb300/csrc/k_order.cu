@@ -21,14 +21,14 @@
 #include <climits>
 #include <mutex>
 
-#include "vl_internal.cuh"
+#include "order_search.cuh"
 
 
 namespace vl {
 
 namespace {
 
-constexpr int OTH = 1024;
+using namespace search;
 static_assert(VL_MAX_M <= 4 * OTH, "ordering holds at most four variables per thread");
 static_assert(VL_MAX_M <= 4096, "the search key holds the variable index in 12 bits");
 
@@ -80,107 +80,6 @@ __global__ void rowsum_kernel(const double* __restrict__ D, int m, float* __rest
   }
 }
 
-// order-preserving map float -> uint32 (valid for every non-NaN value)
-__device__ __forceinline__ uint32_t fkey(float f) {
-  uint32_t b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-// (hi, lo) -= (ph, pl) in double-float, renormalised so |lo| <= ulp(hi)/2
-// (then the pair order equals the order of (key(hi), key(lo))).
-__device__ __forceinline__ void df_sub(float& hi, float& lo, float ph, float pl) {
-  float s = hi - ph;
-  float bp = s - hi;
-  float err = (hi - (s - bp)) + (-ph - bp);
-  float l = lo - pl + err;
-  float h2 = s + l;
-  lo = l - (h2 - s);
-  hi = h2;
-}
-
-// clock64 read ordered after `dep` is available
-__device__ __forceinline__ long long clock_after(float dep) {
-  long long t;
-  asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : "f"(dep));
-  return t;
-}
-
-
-// Search key of a live variable: (fkey(hi), fkey(lo) with its low 12 bits
-// replaced by the index).  Compared as a 64-bit integer it orders by the
-// double-float score and then by index; dropping 12 bits of lo merges
-// scores closer than about 2^-35 relative into index order, far below any
-// gap the method distinguishes.  A dead variable is (~0, ~0).
-__device__ __forceinline__ uint2 skey(float hi, float lo, int i) {
-  return make_uint2(fkey(hi), (fkey(lo) & 0xfffff000u) | (uint32_t)i);
-}
-// warp-wide minimum key, in every lane (two REDUX, no branches)
-__device__ __forceinline__ uint2 warp_kmin(uint2 k) {
-  const uint32_t full = 0xffffffffu;
-  const uint32_t h = __reduce_min_sync(full, k.x);
-  const uint32_t l = __reduce_min_sync(full, k.x == h ? k.y : 0xffffffffu);
-  return make_uint2(h, l);
-}
-
-// The search, one CTA of up to 1024 threads, each owning PER variables
-// (i = tid + q*nthr).  A step: every warp reduces its keys (warp_kmin) and
-// lane 0 writes the warp minimum to a shared slot of the step's parity; one
-// barrier; every warp then reduces the warp minima itself, so all threads
-// learn the pick c without a second barrier (slots alternate by parity: a
-// warp can run at most one step ahead of the slowest); S_i -= P_{i,c}.  (A
-// prefetch of the likely runner-up's column was measured to cost more than
-// it saved once the reductions were branch-free.)  fetch(c, i, h, l) loads
-// P_{i,c} as the double-float pair (h, l).  prof (optional, NULL in the
-// library): clock64 stamps of thread 0, five per step: start, warp minimum
-// written, after the barrier, pick known, update done.
-template <int PER, class Fetch>
-__device__ __forceinline__ void search_steps(float (&hi)[PER], float (&lo)[PER],
-                                             bool (&alive)[PER], int m,
-                                             int32_t* __restrict__ order,
-                                             long long* __restrict__ prof, Fetch fetch) {
-  __shared__ uint2 wb[2][32];
-  const int nthr = blockDim.x, nw = (nthr + 31) >> 5;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint2 dead = make_uint2(0xffffffffu, 0xffffffffu);
-  for (int k = 0; k < m; ++k) {
-    const int ph = k & 1;
-    if (prof && threadIdx.x == 0) prof[5 * k] = clock64();
-    uint2 b = dead;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const uint2 c = alive[q] ? skey(hi[q], lo[q], (int)threadIdx.x + q * nthr) : dead;
-      if (c.x < b.x || (c.x == b.x && c.y < b.y)) b = c;
-    }
-    const uint2 w = warp_kmin(b);
-    if (lane == 0) wb[ph][wid] = w;
-    if (prof && threadIdx.x == 0) prof[5 * k + 1] = clock64();
-    __syncthreads();
-    if (prof && threadIdx.x == 0) prof[5 * k + 2] = clock64();
-    // block level, redundantly in every warp
-    const uint2 a = lane < nw ? wb[ph][lane] : dead;
-    const uint2 g = warp_kmin(a);
-    const int c = (int)(g.y & 0xfffu);
-    if (prof && threadIdx.x == 0) prof[5 * k + 3] = clock64();
-    if (threadIdx.x == 0) order[k] = c;
-    float ch[PER], cl[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      ch[q] = cl[q] = 0.f;
-      if (alive[q]) fetch(c, (int)threadIdx.x + q * nthr, ch[q], cl[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int i = threadIdx.x + q * nthr;
-      if (!alive[q]) continue;
-      if (i == c)
-        alive[q] = false;
-      else
-        df_sub(hi[q], lo[q], ch[q], cl[q]);
-    }
-    if (prof && threadIdx.x == 0) prof[5 * k + 4] = clock_after(hi[0]);
-  }
-}
-
 // Search with P in global memory (L2): Pt_hi/lo[c * m + i] = P_{i,c}.
 template <int PER>
 __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pth,
@@ -188,6 +87,7 @@ __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pt
                                                     const float* __restrict__ sh0,
                                                     const float* __restrict__ sl0, int m,
                                                     int32_t* __restrict__ order,
+                                                    double* __restrict__ spick,
                                                     long long* __restrict__ prof) {
   float hi[PER], lo[PER];
   bool alive[PER];
@@ -198,20 +98,11 @@ __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pt
     hi[q] = alive[q] ? sh0[i] : 0.f;
     lo[q] = alive[q] ? sl0[i] : 0.f;
   }
-  search_steps<PER>(hi, lo, alive, m, order, prof, [&](int c, int i, float& h, float& l) {
+  search_steps<PER>(hi, lo, alive, m, 0, -1, order, spick, prof,
+                    [&](int c, int i, float& h, float& l) {
     h = pth[(int64_t)c * m + i];
     l = ptl[(int64_t)c * m + i];
   });
-}
-
-// order-preserving map double -> uint64
-__device__ __forceinline__ unsigned long long dkey(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double dkey_inv(unsigned long long k) {
-  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
-  return __longlong_as_double((long long)b);
 }
 
 // Gaps after the search, from the order: variable i replays its score
@@ -261,42 +152,52 @@ __global__ void gap_kernel(const double* __restrict__ s1, const unsigned long lo
 
 }  // namespace
 
+OrderWs order_ws_layout(void* ws, int m) {
+  OrderWs w;
+  char* p = static_cast<char*>(ws);
+  w.pth = reinterpret_cast<float*>(p);
+  w.ptl = w.pth + (size_t)m * m;
+  w.sh = w.ptl + (size_t)m * m;
+  w.sl = w.sh + m;
+  w.s1 = reinterpret_cast<double*>(((uintptr_t)(w.sl + m) + 15) & ~(uintptr_t)15);
+  w.s2 = reinterpret_cast<unsigned long long*>(w.s1 + m);
+  return w;
+}
+
+void launch_order_gaps(void* ws, int m, const int32_t* order, double* gap, cudaStream_t s) {
+  const OrderWs w = order_ws_layout(ws, m);
+  cudaMemsetAsync(w.s2, 0xff, (size_t)m * sizeof(unsigned long long), s);
+  note_launch();
+  gap_scores_kernel<<<(m + 127) / 128, 128, 0, s>>>(w.pth, w.ptl, w.sh, w.sl, order, m, w.s1,
+                                                      w.s2);
+  note_launch();
+  gap_kernel<<<(m + 255) / 256, 256, 0, s>>>(w.s1, w.s2, m, gap);
+}
+
 size_t order_ws_bytes(int m) {
   return (size_t)m * m * 2 * sizeof(float) + (size_t)m * 2 * sizeof(float) +
          (size_t)m * sizeof(float4) + 1024;
 }
 
 void launch_causal_order(const double* D, int m, void* ws, int32_t* order, double* gap, int* st,
-                         cudaStream_t s, long long* prof) {
-  char* p = static_cast<char*>(ws);
-  float* pth = reinterpret_cast<float*>(p);
-  float* ptl = pth + (size_t)m * m;
-  float* sh = ptl + (size_t)m * m;
-  float* sl = sh + m;
-  double* s1 = reinterpret_cast<double*>(((uintptr_t)(sl + m) + 15) & ~(uintptr_t)15);
-  unsigned long long* s2 = reinterpret_cast<unsigned long long*>(s1 + m);
+                         cudaStream_t s, long long* prof, double* spick) {
+  const OrderWs w = order_ws_layout(ws, m);
   dim3 grid((m + 31) / 32, (m + 31) / 32), block(32, 8);
   note_launch();
-  pt_kernel<<<grid, block, 0, s>>>(D, m, pth, ptl, st);
+  pt_kernel<<<grid, block, 0, s>>>(D, m, w.pth, w.ptl, st);
   note_launch();
-  rowsum_kernel<<<(m + 7) / 8, 256, 0, s>>>(D, m, sh, sl);
+  rowsum_kernel<<<(m + 7) / 8, 256, 0, s>>>(D, m, w.sh, w.sl);
   // variables per thread: PER = 1 up to 1024 variables, then 2 and 4
   const int per = m <= OTH ? 1 : (m <= 2 * OTH ? 2 : 4);
   const int nthr = std::min(OTH, ((m + per - 1) / per + 31) / 32 * 32);
   note_launch();
   if (per == 1)
-    order_kernel<1><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, prof);
+    order_kernel<1><<<1, nthr, 0, s>>>(w.pth, w.ptl, w.sh, w.sl, m, order, spick, prof);
   else if (per == 2)
-    order_kernel<2><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, prof);
+    order_kernel<2><<<1, nthr, 0, s>>>(w.pth, w.ptl, w.sh, w.sl, m, order, spick, prof);
   else
-    order_kernel<4><<<1, nthr, 0, s>>>(pth, ptl, sh, sl, m, order, prof);
-  if (gap) {
-    cudaMemsetAsync(s2, 0xff, (size_t)m * sizeof(unsigned long long), s);
-    note_launch();
-    gap_scores_kernel<<<(m + 127) / 128, 128, 0, s>>>(pth, ptl, sh, sl, order, m, s1, s2);
-    note_launch();
-    gap_kernel<<<(m + 255) / 256, 256, 0, s>>>(s1, s2, m, gap);
-  }
+    order_kernel<4><<<1, nthr, 0, s>>>(w.pth, w.ptl, w.sh, w.sl, m, order, spick, prof);
+  if (gap) launch_order_gaps(ws, m, order, gap, s);
 }
 
 }  // namespace vl

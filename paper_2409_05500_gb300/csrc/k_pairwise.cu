@@ -150,17 +150,19 @@ __device__ __forceinline__ void end_run2(Pair2& q) {
 
 // MTI x 2 pair micro-tiles, (32 / MTI) x 16 threads per 32 x 32 tile, TTS
 // samples per shared-memory stage, MINB CTAs per SM.
-template <int MTI, int TTS, int MINB>
-__global__ void __launch_bounds__(TB / MTI * 16, MINB)
-    pairwise_f32_kernel(const float* __restrict__ xt, int m, int m_pad, int T, int n_run,
-                        int tps, const float* __restrict__ rho32,
-                        const float* __restrict__ c32, float* __restrict__ part) {
+// One work item: pair tile `tile` of the upper triangle, sample split `split`.
+template <int MTI, int TTS>
+__device__ __forceinline__ void pairwise_f32_item(int tile, int split,
+                                                  const float* __restrict__ xt, int m, int m_pad,
+                                                  int T, int n_run, int tps,
+                                                  const float* __restrict__ rho32,
+                                                  const float* __restrict__ c32,
+                                                  float* __restrict__ part) {
   constexpr int NT = TB / MTI * 16;
   extern __shared__ __align__(16) float pw_smem[];
   float(*sx)[TTS][2 * TB] = reinterpret_cast<float(*)[TTS][2 * TB]>(pw_smem);  // [3][TTS][64]
   int I, J;
-  tile_coords(blockIdx.x, T, I, J);
-  const int split = blockIdx.y;
+  tile_coords(tile, T, I, J);
   const int t0 = split * tps;
   const int t1 = min(n_run, t0 + tps);
 
@@ -269,6 +271,31 @@ __global__ void __launch_bounds__(TB / MTI * 16, MINB)
         base[3 * mm] = -(b ? st.cb.y : st.cb.x);
       }
     }
+  }
+}
+
+template <int MTI, int TTS, int MINB>
+__global__ void __launch_bounds__(TB / MTI * 16, MINB)
+    pairwise_f32_kernel(const float* __restrict__ xt, int m, int m_pad, int T, int n_run,
+                        int tps, const float* __restrict__ rho32,
+                        const float* __restrict__ c32, float* __restrict__ part) {
+  pairwise_f32_item<MTI, TTS>(blockIdx.x, blockIdx.y, xt, m, m_pad, T, n_run, tps, rho32, c32,
+                              part);
+}
+
+// Many instances in one launch: a device list of (job, tile, split) items,
+// ordered by cost (largest first), dealt round-robin to a grid of about one
+// CTA per SM; each CTA runs its items one after another.
+template <int MTI, int TTS, int MINB>
+__global__ void __launch_bounds__(TB / MTI * 16, MINB)
+    pairwise_f32_list_kernel(const PairJob* __restrict__ jobs, const int4* __restrict__ items,
+                             int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 w = items[it];
+    const PairJob& j = jobs[w.x];
+    pairwise_f32_item<MTI, TTS>(w.y, w.z, j.xt, j.m, j.m_pad, j.T, j.n_run, j.tps, j.rho32,
+                                j.c32, j.part);
+    __syncthreads();  // the sample stages are reused by the next item
   }
 }
 
@@ -463,6 +490,23 @@ PairPlan plan_pairwise_slots(int m, int n, int slots, int tts, bool fp64, int nu
   return pl;
 }
 
+PairPlan plan_pairwise_split(int m, int n, int split_len) {
+  PairPlan pl{};
+  pl.m = m;
+  pl.n = n;
+  pl.m_pad = ((m + TB - 1) / TB) * TB;
+  const int Tside = pl.m_pad / TB;
+  pl.tiles = Tside * (Tside + 1) / 2;
+  const int n_run = ((n + KRUN - 1) / KRUN) * KRUN;
+  int tps = std::max(KRUN, ((std::min(split_len, n_run) + KRUN - 1) / KRUN) * KRUN);
+  pl.splits = (n_run + tps - 1) / tps;
+  tps = ((n_run + pl.splits - 1) / pl.splits + KRUN - 1) / KRUN * KRUN;  // even splits
+  pl.splits = (n_run + tps - 1) / tps;
+  pl.t_per_split = tps;
+  pl.n_pad = ((n_run + 255) / 256) * 256;
+  return pl;
+}
+
 PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64) {
   return plan_pairwise_slots(m, n, F32_MINB * num_sms, F32_TTS, fp64, num_sms);
 }
@@ -494,6 +538,36 @@ void launch_pairwise_f32_cfg(const float* xt, const PairPlan& pl, const float* r
 void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32,
                          const float* c32, float* part, cudaStream_t s) {
   launch_pairwise_f32_cfg<F32_MTI, F32_TTS, F32_MINB>(xt, pl, rho32, c32, part, s);
+}
+
+PairJob make_pair_job(const float* xt, const PairPlan& pl, const float* rho32, const float* c32,
+                      float* part) {
+  PairJob j;
+  j.xt = xt;
+  j.rho32 = rho32;
+  j.c32 = c32;
+  j.part = part;
+  j.m = pl.m;
+  j.m_pad = pl.m_pad;
+  j.T = pl.m_pad / TB;
+  j.n_run = ((pl.n + KRUN - 1) / KRUN) * KRUN;
+  j.tps = pl.t_per_split;
+  return j;
+}
+
+void launch_pairwise_f32_list(const PairJob* jobs, const int4* items, int nitems, int grid,
+                              cudaStream_t s) {
+  constexpr int MTI = F32_MTI, TTS = F32_TTS, MINB = F32_MINB;
+  const size_t smem = sizeof(float) * 3 * TTS * 2 * TB;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(pairwise_f32_list_kernel<MTI, TTS, MINB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  note_launch();
+  pairwise_f32_list_kernel<MTI, TTS, MINB><<<std::max(1, std::min(grid, nitems)), TB / MTI * 16,
+                                             smem, s>>>(jobs, items, nitems);
 }
 
 void launch_pairwise_f64(const double* xt, const PairPlan& pl, const double* rho64,

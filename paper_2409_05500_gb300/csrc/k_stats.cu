@@ -74,12 +74,18 @@ __global__ void __launch_bounds__(kStatThreads) var_prep_kernel(
 template <class T>
 __global__ void var_normal_eq_kernel(const double* __restrict__ G, int m, int p, int n_eff,
                                      const double* __restrict__ wbar, T* __restrict__ Gzz,
-                                     T* __restrict__ Gzy) {
+                                     T* __restrict__ Gzy, float* __restrict__ nhi,
+                                     float* __restrict__ nlo) {
   const int mp = m * p, q = m * (p + 1);
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)mp * q) return;
   const int a = (int)(idx / q), b = (int)(idx % q);
   const double v = G[idx] - (double)n_eff * wbar[m + a] * wbar[b];
+  if (nhi) {  // the same values as an FP32 pair, for the refinement residual
+    const float h = (float)v;
+    nhi[idx] = h;
+    nlo[idx] = (float)(v - (double)h);
+  }
   if (b < m)
     Gzy[(int64_t)a * m + b] = (T)v;
   else
@@ -260,17 +266,17 @@ template void launch_var_prep<double>(const double*, int64_t, int, int, int, dou
 
 template <class T>
 void launch_var_normal_eq(const double* G, int m, int p, int n_eff, const double* wbar, T* Gzz,
-                          T* Gzy, cudaStream_t s) {
+                          T* Gzy, cudaStream_t s, float* nhi, float* nlo) {
   const int mp = m * p;
   const int64_t tot = (int64_t)mp * (mp + m);
   note_launch();
   var_normal_eq_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, m, p, n_eff, wbar,
-                                                                        Gzz, Gzy);
+                                                                        Gzz, Gzy, nhi, nlo);
 }
 template void launch_var_normal_eq<float>(const double*, int, int, int, const double*, float*,
-                                          float*, cudaStream_t);
+                                          float*, cudaStream_t, float*, float*);
 template void launch_var_normal_eq<double>(const double*, int, int, int, const double*,
-                                           double*, double*, cudaStream_t);
+                                           double*, double*, cudaStream_t, float*, float*);
 
 template <class T>
 void launch_var_coef(const T* beta, int m, int p, const double* wbar, double* M, double* cst,
@@ -283,6 +289,13 @@ void launch_var_coef(const T* beta, int m, int p, const double* wbar, double* M,
 }
 template void launch_var_coef<float>(const float*, int, int, const double*, double*, double*,
                                      cudaStream_t);
+
+template <class T>
+void launch_var_cst(const T* beta, int m, int p, const double* wbar, double* cst, cudaStream_t s) {
+  note_launch();
+  var_cst_kernel<T><<<(m + 7) / 8, 256, 0, s>>>(beta, m, p, wbar, cst);
+}
+template void launch_var_cst<float>(const float*, int, int, const double*, double*, cudaStream_t);
 template void launch_var_coef<double>(const double*, int, int, const double*, double*, double*,
                                       cudaStream_t);
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/varlingam_gb300.h"
@@ -80,6 +81,16 @@ struct vl_handle_s {
   cudaEvent_t prof_start = nullptr;  // optional: recorded around the pairwise kernel
   cudaEvent_t prof_stop = nullptr;
   std::string last_error;
+  // phase-major batches (mixed precision): per-instance buffers, the device
+  // list of pairwise work items of the last batch layout and its signature,
+  // and the autotuner's cache (batch signature -> samples per split)
+  void* bbuf = nullptr;
+  size_t bbuf_cap = 0;
+  void* blist = nullptr;
+  size_t blist_cap = 0;
+  unsigned long long blist_sig = 0;
+  int blist_items = 0;
+  std::unordered_map<unsigned long long, int> split_tune;
 };
 
 namespace vl {
@@ -110,14 +121,25 @@ void launch_var_prep(const double* X, int64_t ldx, int m, int n, int p, T* Xc, i
 // VAR normal equations from the lagged Gram G (mp x m(p+1), FP64, uncentred
 // in the windows): Gzz = centred Z Z^T (T, mp x mp), Gzy = centred Z Y^T
 // (T, mp x m).
+// nhi / nlo (optional, mp x m(p+1)): the centred normal equations as FP32
+// pairs, for the refinement residual (k_refine.cu).
 template <class T>
 void launch_var_normal_eq(const double* G, int m, int p, int n_eff, const double* wbar, T* Gzz,
-                          T* Gzy, cudaStream_t s);
+                          T* Gzy, cudaStream_t s, float* nhi = nullptr, float* nlo = nullptr);
 // M[tau][i][k] = beta[(tau-1) m + k][i]; cst[i] = intercept offset of row i;
 // E[i][t] = X[i][p + t] - mu_i - cst_i (the GEMM then subtracts sum M Z).
 template <class T>
 void launch_var_coef(const T* beta, int m, int p, const double* wbar, double* M, double* cst,
                      cudaStream_t s);
+template <class T>
+void launch_var_cst(const T* beta, int m, int p, const double* wbar, double* cst, cudaStream_t s);
+// One refinement step of the VAR coefficients (k_refine.cu): r = G_zy -
+// G_zz beta0 in double-float from the FP32 pairs (nhi, nlo); after the FP32
+// correction solve, beta = beta0 + delta into M (FP64) and beta0 (FP32).
+void launch_refine_residual(const float* nhi, const float* nlo, int m, int p, const float* beta0,
+                            float* r, cudaStream_t s);
+void launch_refine_apply(float* beta, const float* delta, int m, int p, double* M,
+                         cudaStream_t s);
 void launch_var_resid_init(const double* X, int64_t ldx, int m, int n, int p, const double* mu,
                            const double* cst, double* E, int64_t lde, cudaStream_t s);
 template <class T>
@@ -181,19 +203,72 @@ struct PairPlan {
   int m, n, m_pad, n_pad, tiles, splits, t_per_split;
 };
 PairPlan plan_pairwise(int m, int n, int num_sms, bool fp64);
+// FP32 plan with sample splits of about split_len samples (batched launches,
+// where many instances fill the GPU together)
+PairPlan plan_pairwise_split(int m, int n, int split_len);
 void launch_pair_consts(const double* C, int m, float* rho32, float* c32, double* rho64, int* st,
                         cudaStream_t s);
 void launch_pairwise_f32(const float* xt, const PairPlan& pl, const float* rho32,
                          const float* c32, float* part, cudaStream_t s);
 void launch_pairwise_f64(const double* xt, const PairPlan& pl, const double* rho64,
                          double* part, cudaStream_t s);
+// One instance of the FP32 pairwise kernel in a multi-instance launch.
+struct PairJob {
+  const float* xt;
+  const float* rho32;
+  const float* c32;
+  float* part;
+  int m, m_pad, T, n_run, tps;
+};
+PairJob make_pair_job(const float* xt, const PairPlan& pl, const float* rho32, const float* c32,
+                      float* part);
+// items: (job, tile, split, 0), largest first; grid: CTAs (about one per SM)
+void launch_pairwise_f32_list(const PairJob* jobs, const int4* items, int nitems, int grid,
+                              cudaStream_t s);
 void launch_measure_finalize(const void* part, const PairPlan& pl, const double* hx_mom,
                              double* Hx, double* Hr, double* D, bool fp32_parts, cudaStream_t s);
 
-// Ordering (k_order.cu)
+// Ordering (k_order.cu).  Its workspace: P^T as double-float (pth, ptl),
+// the initial row sums (sh, sl) and the gap scratch (s1, s2).
+struct OrderWs {
+  float *pth, *ptl, *sh, *sl;
+  double* s1;
+  unsigned long long* s2;
+};
+OrderWs order_ws_layout(void* ws, int m);
 size_t order_ws_bytes(int m);
+// per-step relative gaps of an order over the workspace's P (after a search)
+void launch_order_gaps(void* ws, int m, const int32_t* order, double* gap, cudaStream_t s);
+// spick (optional): the winning score of every step, for the certification
+// of near ties (k_certify.cu).
 void launch_causal_order(const double* D, int m, void* ws, int32_t* order, double* gap, int* st,
-                         cudaStream_t s, long long* prof = nullptr);
+                         cudaStream_t s, long long* prof = nullptr, double* spick = nullptr);
+
+// Tensor-core exact-slice Gram products (k_tcgram.cu).  Operands are three
+// bf16 slice planes S[z][r][k] (k < Kpad = tg_kpad(K), a multiple of 64; row
+// stride Kpad, plane stride `plane` elements) with a power-of-two exponent
+// per row.  slice_center: rows E[r] - mu[r] (FP64); slice_lags: the lag
+// windows of the centred FP32 series Xc, row b m + k = Xc[k][p - b + t].
+// launch_tcgram_sym: C = (S S^T) scaled back, N x N FP64 symmetric, using
+// the context's split-K scratch; false if the tensor maps cannot be made.
+int64_t tg_kpad(int K);
+void launch_slice_center(const double* E, int64_t lde, const double* mu, int m, int K,
+                         int64_t Kpad, void* S, int64_t plane, int* exps, cudaStream_t s);
+void launch_slice_lags(const float* Xc, int64_t ldc, int m, int n, int p, int64_t Kpad, void* S,
+                       int64_t plane, int* exps, cudaStream_t s);
+bool launch_tcgram_sym(const Ctx& cx, const void* S, int N, int Kpad, int64_t ldo, int64_t plane,
+                       const int* exps, double* C, int64_t ldc);
+
+// Certified ordering (k_certify.cu): after a search on an FP32-measure D
+// (launch_causal_order with spick = certify_spick(cert_ws, m)), near ties
+// are re-decided on FP64 entries of D computed from E (m x n, lde).
+// stats_out (device, 4 ints, may be NULL): flagged steps, pairs re-evaluated,
+// picks changed, steps left unverified.
+size_t certify_ws_bytes(int m);
+double* certify_spick(void* cert_ws, int m);
+void launch_certify(const double* D, const double* E, int64_t lde, int m, int n, void* order_ws,
+                    void* cert_ws, int32_t* order, int32_t* stats_out, int num_sms,
+                    cudaStream_t s);
 
 // Iterative search of Sec. 3 (k_standard.cu).  score_pick: Eq. 3 over the
 // u x u measure D, argmin (ties: lowest index) into *pick, order[k] =

@@ -82,6 +82,8 @@ def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
         "vl_pairwise_measure": ([P, P, I64, I, I, I, P, P, P],
                                 [None, None, 100, 10, 100, 1, None, None, None]),
         "vl_causal_order": ([P, P, I, P, P], [None, None, 10, None, None]),
+        "vl_causal_order_certified": ([P, P, P, I64, I, I, P, P, P],
+                                      [None, None, None, 100, 10, 100, None, None, None]),
         "vl_causal_order_standard": ([P, P, I64, I, I, I, P, P],
                                      [None, None, 100, 10, 100, 1, None, None]),
         "vl_fit_b": ([P, P, I64, I, I, P, P, I, I, P, P],
@@ -89,10 +91,11 @@ def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
         "vl_fit": ([P, P, I64, I, I, I, I, P, P, P, P, P],
                    [None, None, 100, 10, 100, 1, 1, None, None, None, None, None]),
         "vl_fit_batched": ([P, P, I, I, P], [None, None, 1, 1, None]),
+        "vl_fit_batched_async": ([P, P, I, I, P], [None, None, 1, 1, None]),
     }
     handle_calls = [n for n in declared_functions()
                     if n not in ("vl_create", "vl_kernel_launches", "vl_last_error",
-                                 "vl_causal_order_noalloc")]
+                                 "vl_causal_order_noalloc", "vl_sfu_rate")]
     assert sorted(handle_calls) == sorted(calls)
     lib.vl_kernel_launches.restype = ctypes.c_ulonglong
     lib.vl_kernel_launches.argtypes = []
@@ -110,4 +113,8 @@ def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
     assert f(None, None, 4, None, None) == 1              # VL_ERR_ARG
     assert f(None, ctypes.addressof(buf), 0, ctypes.addressof(order), None) == 2   # VL_ERR_SHAPE
     assert f(None, ctypes.addressof(buf), 513, ctypes.addressof(order), None) == 9  # UNSUPPORTED
+    f = lib.vl_sfu_rate
+    f.argtypes = [I, P, P]
+    f.restype = I
+    assert f(0, None, None) == 1                          # VL_ERR_ARG
     assert lib.vl_kernel_launches() == launches0          # none of these launched anything

@@ -1,0 +1,145 @@
+"""GPU parity at full size against stored oracle values: all 256 series of the
+mixed-size batch through vl_fit_batched, and the finance-shaped stretch
+series (m = 800 and 1600, n = 5000) through the step-by-step calls.
+
+The stored values (tests/golden/*_oracle.json.gz) were written by
+tests/golden/make_golden.py from the FP64 oracle alone: per series the whole
+Algorithm 1 order with every step's relative score gap, all variable
+entropies, and seeded samples of D, E_r, M, B0 and B_tau.
+
+Tolerances as in test_gpu_parity.py: D within 1e-5 of max|D|, H within 1e-5
+of max(|H|, H_nu), M within 1e-5, B0 and B_tau within 1e-4 absolute; the
+order identical to the oracle's at every step before the first step whose
+oracle gap is <= 1e-6 (from there on, the samples of B0 only hold for the
+oracle's order and are not compared).  The certified mixed path meets the
+order rule; the plain mixed path is also run and its agreement reported.
+"""
+import gzip
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+D_REL, H_REL, B_ABS, M_ABS, GAP = 1e-5, 1e-5, 1e-4, 1e-5, 1e-6
+
+
+def _load(name):
+    with gzip.open(os.path.join(GOLDEN, name), "rt") as f:
+        return json.load(f)
+
+
+def _report(key, **vals):
+    out = os.environ.get("VL_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "parity_errors.jsonl"), "a") as f:
+            f.write(json.dumps({"case": key, **{k: float(v) for k, v in vals.items()}}) + "\n")
+
+
+def _order_prefix(g):
+    """Steps before the first oracle near tie (gap <= 1e-6), and whether there
+    is none at all (then the whole order must be identical)."""
+    gaps = g["gaps"]
+    for k, v in enumerate(gaps):
+        if v <= GAP:
+            return k, False
+    return len(g["order"]), True
+
+
+def _check_series(g, order, D, M, B0, Bt, Hx=None, Hr=None):
+    """Returns the per-series errors; asserts the tolerances."""
+    m = g["m"]
+    assert sorted(order.tolist()) == list(range(m))
+    k, whole = _order_prefix(g)
+    same = order[:k].tolist() == g["order"][:k]
+    assert same, ("order differs before the first oracle near tie", k)
+    dmax = g["D_maxabs"]
+    d_err = max(abs(D[i, j] - v) for i, j, v in g["D"]) / dmax
+    assert d_err <= D_REL, d_err
+    m_err = max(abs(M[t, i, kk] - v) for t, i, kk, v in g["M"])
+    assert m_err <= M_ABS, m_err
+    errs = {"d_rel": d_err, "m_err": m_err, "prefix": k}
+    if whole:
+        b_err = max(abs(B0[i, j] - v) for i, j, v in g["B0"])
+        t_err = max(abs(Bt[t, i, kk] - v) for t, i, kk, v in g["Btau"])
+        assert b_err <= B_ABS and t_err <= B_ABS, (b_err, t_err)
+        errs.update(b0_err=b_err, btau_err=t_err)
+    if Hx is not None:
+        ex = np.array(g["Ex"])
+        hx_err = np.max(np.abs(Hx - ex) / np.maximum(np.abs(ex), oracle.H_GAUSS))
+        hr_err = max(abs(Hr[i, j] - v) / max(abs(v), oracle.H_GAUSS) for i, j, v in g["Er"])
+        assert hx_err <= H_REL and hr_err <= H_REL, (hx_err, hr_err)
+        errs.update(hx=hx_err, hr=hr_err)
+    return errs
+
+
+@pytest.fixture(scope="module")
+def h(vl):
+    handle = vl.Handle(0)
+    yield handle
+    handle.close()
+
+
+def test_batched_all_256_series_against_the_oracle(vl, h):
+    """vl_fit_batched on the 256 seeded series (m 20..400, n 250..5000, p
+    1..3) in certified mixed precision: every series at the oracle's
+    tolerances and order rule.  The plain mixed batch runs too; its orders
+    are reported (they may swap near ties the certified path re-decides)."""
+    gold = _load("batched_oracle.json.gz")["series"]
+    insts = synth.make_batched(256, synth.config_seed(4))
+    assert len(gold) == len(insts) == 256
+    dicts = []
+    for inst, g in zip(insts, gold):
+        assert (inst.m, inst.n, inst.p) == (g["m"], g["n"], g["p"])
+        o = vl.alloc_outputs(inst.m, inst.p)
+        o["X"] = torch.from_numpy(inst.X).cuda()
+        o["p"] = inst.p
+        dicts.append(o)
+    status = vl.vl_fit_batched(h, dicts, "mixed_certified")
+    assert all(s == 0 for s in status), status
+    worst = {}
+    for k, (o, g) in enumerate(zip(dicts, gold)):
+        errs = _check_series(g, o["order"].cpu().numpy(), o["D"].cpu().numpy(),
+                             o["M"].cpu().numpy(), o["B0"].cpu().numpy(),
+                             o["Btau"].cpu().numpy())
+        for key, v in errs.items():
+            worst[key] = max(worst.get(key, 0.0), v) if key != "prefix" else 0.0
+    # the plain mixed batch: how many series keep the oracle's order
+    plain = []
+    for o in dicts:
+        o2 = {key: (torch.empty_like(v) if torch.is_tensor(v) and key != "X" else v)
+              for key, v in o.items()}
+        plain.append(o2)
+    vl.vl_fit_batched(h, plain, "mixed")
+    agree = sum(int(o2["order"].cpu().numpy()[:_order_prefix(g)[0]].tolist()
+                    == g["order"][:_order_prefix(g)[0]]) for o2, g in zip(plain, gold))
+    _report("batched 256 certified", mixed_plain_agree=agree, **worst)
+
+
+@pytest.mark.parametrize("m", [800, 1600])
+@pytest.mark.parametrize("prec", ["mixed_certified", "fp64"])
+def test_stretch_series_against_the_oracle(vl, h, m, prec):
+    """The stretch sizes (finance-shaped, n = 5000): m = 800 runs the
+    one-cluster Cholesky, m = 1600 the blocked multi-kernel one, the
+    two-variables-per-thread ordering and the column-sweep triangular
+    solves."""
+    g = _load(f"stretch_m{m}_oracle.json.gz")["series"][0]
+    inst = synth.make_config("finance", m=m, n=5000)
+    X = torch.from_numpy(inst.X).cuda()
+    out = vl.fit(h, X, inst.p, prec=prec, steps=True)
+    errs = _check_series(g, out["order"].cpu().numpy(), out["D"].cpu().numpy(),
+                         out["M"].cpu().numpy(), out["B0"].cpu().numpy(),
+                         out["Btau"].cpu().numpy(), out["Hx"].cpu().numpy(),
+                         out["Hr"].cpu().numpy())
+    if "cert_stats" in out:
+        st = out["cert_stats"].cpu().numpy()
+        errs.update(flagged=st[0], pairs=st[1], changed=st[2], unverified=st[3])
+    _report(f"stretch m={m} {prec}", **errs)

@@ -6,7 +6,10 @@ Tolerances (written here, used everywhere below):
   Hx, Hr       |dH| <= 1e-5 * max(|H_ref|, H_nu), H_nu = 1.4189 the entropy of
                N(0,1): relative where H is O(1), and relative to the entropy
                scale where a heavy-tailed variable drives H towards zero
-  order        identical wherever the oracle's relative score gap > 1e-6
+  order        identical wherever the oracle's relative score gap > 1e-6 (the
+               FP64 path and the certified mixed path); the plain mixed path
+               is Algorithm 1 exactly on its own D, and against the oracle up
+               to what its D difference explains
   B0, B_tau    1e-4 absolute (B0 from the GPU's order, compared with the
                oracle's predecessor regression on that same order)
   M            1e-5 absolute (mixed) / 1e-9 (FP64)
@@ -70,7 +73,9 @@ def _report(key, **vals):
 def _check_measure(ref, Hx, Hr, D, key="measure"):
     dmax = np.abs(ref["D"]).max()
     off = ~np.eye(D.shape[0], dtype=bool)
+    big = np.abs(ref["D"]) >= 1e-3 * dmax  # elementwise relative error where it is meaningful
     _report(key, d_rel=np.abs(D - ref["D"]).max() / dmax,
+            d_elem_rel=np.max(np.abs(D - ref["D"])[big] / np.abs(ref["D"])[big]),
             hx=np.max(np.abs(Hx - ref["Ex"]) / np.maximum(np.abs(ref["Ex"]), oracle.H_GAUSS)),
             hr=np.max((np.abs(Hr - ref["Er"]) / np.maximum(np.abs(ref["Er"]), oracle.H_GAUSS))[off]))
     assert np.abs(D - ref["D"]).max() <= D_REL * dmax, np.abs(D - ref["D"]).max() / dmax
@@ -138,22 +143,31 @@ def _ref_pipeline(key, inst):
         M, E = oracle.var_ols(inst.X, inst.p)
         meas = oracle.pairwise_measure(oracle.standardize(E))
         od = oracle.order_heuristic(meas["D"])
-        _ref_cache[key] = dict(M=M, E=E, order=od["order"], **meas)
+        gaps = [oracle.relative_gap(st["scores"]) for st in od["steps"][:-1]]
+        _ref_cache[key] = dict(M=M, E=E, order=od["order"], gaps=gaps, **meas)
     return _ref_cache[key]
 
 
 def _check_pipeline(ref, out, prec, p, key="pipeline"):
+    mixed = prec != "fp64"
     M = out["M"].cpu().numpy()
-    assert np.abs(M - ref["M"]).max() <= (1e-5 if prec == "mixed" else 1e-9)
+    assert np.abs(M - ref["M"]).max() <= (1e-5 if mixed else 1e-9)
     E = out["E"].cpu().numpy()
-    assert np.abs(E - ref["E"]).max() <= (1e-5 if prec == "mixed" else 1e-9) * np.abs(ref["E"]).max()
+    assert np.abs(E - ref["E"]).max() <= (1e-5 if mixed else 1e-9) * np.abs(ref["E"]).max()
     _check_measure(ref, out["Hx"].cpu().numpy(), out["Hr"].cpu().numpy(), out["D"].cpu().numpy(),
                    key=key)
     order = out["order"].cpu().numpy()
-    # Algorithm 1 exactly on the GPU's own D, and the oracle's order up to
-    # what the (tolerated) difference of the two D explains
-    assert oracle.order_gap_ok(order, out["D"].cpu().numpy(), GAP)[0]
-    ok, ties, bad = oracle.order_gap_ok(order, ref["D"], GAP, D_cand=out["D"].cpu().numpy())
+    if prec == "mixed":
+        # Algorithm 1 exactly on the GPU's own D, and the oracle's order up to
+        # what the (tolerated) difference of the two D explains
+        assert oracle.order_gap_ok(order, out["D"].cpu().numpy(), GAP)[0]
+        ok, ties, bad = oracle.order_gap_ok(order, ref["D"], GAP, D_cand=out["D"].cpu().numpy())
+    else:
+        # the strict rule: a minimiser of the oracle's scores at every step
+        # whose oracle gap exceeds 1e-6, identical where no gap is that small
+        ok, ties, bad = oracle.order_gap_ok(order, ref["D"], GAP)
+        if min(ref["gaps"]) > GAP:
+            assert [int(c) for c in order] == [int(c) for c in ref["order"]]
     B0_ref_o = oracle.b0_ols(ref["E"], order)
     _report(key + " order/B", near_ties=ties, identical=float(np.array_equal(order, ref["order"])),
             m_err=np.abs(M - ref["M"]).max(),
@@ -165,7 +179,7 @@ def _check_pipeline(ref, out, prec, p, key="pipeline"):
     assert np.abs(out["Btau"].cpu().numpy() - Bt_ref).max() <= B_ABS
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "mixed_certified", "fp64"])
 @pytest.mark.parametrize("name", ["pr1", "fmri"])
 def test_pipeline_small_workloads(vl, h, prec, name):
     inst = synth.make_config(name)
@@ -174,7 +188,7 @@ def test_pipeline_small_workloads(vl, h, prec, name):
     _check_pipeline(ref, out, prec, inst.p, key=f"{name} {prec}")
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "mixed_certified", "fp64"])
 def test_pipeline_server_workload(vl, h, prec):
     inst = synth.make_config("server")  # m=120, n=10000, p=3
     ref = _ref_pipeline("server", inst)
@@ -182,7 +196,7 @@ def test_pipeline_server_workload(vl, h, prec):
     _check_pipeline(ref, out, prec, inst.p, key=f"server {prec}")
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "mixed_certified", "fp64"])
 def test_pipeline_finance_workload(vl, h, prec):
     inst = synth.make_config("finance")  # m=400, n=2500, p=1
     ref = _ref_pipeline("finance", inst)
@@ -231,10 +245,14 @@ def test_fused_call_replays_from_a_cuda_graph(vl, prec):
         h.close()
 
 
-def test_batched_mixed_sizes_match_single_calls(vl, h):
+@pytest.mark.parametrize("prec", ["mixed_certified", "fp64"])
+def test_batched_mixed_sizes_match_single_calls(vl, h, prec):
     """A batch of series of different (m, n, p), one of them ill-posed: every
-    valid instance equals its single fused call; the bad one reports its own
-    status and does not disturb the others."""
+    valid instance matches its single fused call (the FP64 batch exactly; the
+    phase-major mixed batch splits the samples of the pairwise kernel
+    differently, so D agrees to 1e-6 of max|D| and the certified orders are
+    identical); the bad one reports its own status and does not disturb the
+    others."""
     insts = synth.make_batched(12, 777, max_m=60, max_n=1500)
     outs, dicts = [], []
     for inst in insts:
@@ -245,15 +263,53 @@ def test_batched_mixed_sizes_match_single_calls(vl, h):
     bad = dict(dicts[3])
     bad["X"] = bad["X"][:, : insts[3].m].contiguous()  # n - p <= m p + 1
     dicts_b = dicts[:3] + [bad] + dicts[4:]
-    status = vl.vl_fit_batched(h, dicts_b, "mixed")
+    status = vl.vl_fit_batched(h, dicts_b, prec)
     assert status[3] == 3 and all(s == 0 for k, s in enumerate(status) if k != 3)
+    exact = prec == "fp64"
     for k, inst in enumerate(insts):
         if k == 3:
             continue
-        ref = vl.fit(h, dicts[k]["X"], inst.p, prec="mixed")
+        ref = vl.fit(h, dicts[k]["X"], inst.p, prec=prec)
         assert torch.equal(ref["order"], dicts_b[k]["order"])
-        assert (ref["B0"] - dicts_b[k]["B0"]).abs().max().item() <= 1e-9
-        assert (ref["D"] - dicts_b[k]["D"]).abs().max().item() <= 1e-12
+        dmax = ref["D"].abs().max().item()
+        assert (ref["D"] - dicts_b[k]["D"]).abs().max().item() <= (1e-12 if exact else 1e-6 * dmax)
+        assert (ref["B0"] - dicts_b[k]["B0"]).abs().max().item() <= (1e-9 if exact else 1e-6)
+
+
+def test_batched_async_replays_from_a_cuda_graph(vl):
+    """After one call, the phase-major batch allocates, uploads and tunes
+    nothing: captured into one CUDA graph and replayed on new data of the
+    same shapes, it gives the results of an eager call on that data."""
+    insts = synth.make_batched(10, 4242, max_m=50, max_n=900)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = vl.Handle(stream=stream)
+        dicts = []
+        for inst in insts:
+            o = vl.alloc_outputs(inst.m, inst.p)
+            o["X"] = torch.from_numpy(inst.X).cuda()
+            o["p"] = inst.p
+            dicts.append(o)
+        st = torch.zeros(len(insts), dtype=torch.int32, device="cuda")
+        vl.vl_fit_batched_async(h, dicts, "mixed", st)
+        h.sync()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            vl.vl_fit_batched_async(h, dicts, "mixed", st)
+        rng = np.random.default_rng(9)
+        for rep in range(2):
+            for o, inst in zip(dicts, insts):
+                o["X"].copy_(torch.from_numpy(inst.X + 0.05 * rep * rng.standard_normal(inst.X.shape)))
+            g.replay()
+            stream.synchronize()
+            assert int(st.abs().sum().item()) == 0
+            got = [{k: o[k].clone() for k in ("order", "D", "B0", "M")} for o in dicts]
+            vl.vl_fit_batched_async(h, dicts, "mixed", st)
+            h.sync()
+            for a, o in zip(got, dicts):
+                for k in ("order", "D", "B0", "M"):
+                    assert torch.equal(a[k], o[k]), k
+        h.close()
 
 
 # ------------------------------------- iterative search (Section 3, Eq. 4)
@@ -477,3 +533,94 @@ def test_batched_workload_parity(vl, h):
         _report(f"batched #{k} m={inst.m} n={inst.n} p={inst.p}",
                 d_rel=np.abs(D - ref["D"]).max() / dmax, near_ties=ties,
                 b0_err=np.abs(o["B0"].cpu().numpy() - B0_ref).max())
+
+
+# ------------------------------------------- certified ordering (near ties)
+def _planted_near_tie(D, order_ref, steps, k_pick=None):
+    """A copy of D in which the oracle's next pick b = order[k+1] overtakes
+    the pick a = order[k] at step k by 3e-4 relative: the negative entries of
+    row b are scaled so that b's step-k score is a's times (1 - 3e-4).  Only
+    row b's own score changes (column b is untouched), so b stays the pick
+    of step k + 1 and every other step is as before."""
+    best = None
+    for k in range(len(order_ref) - 2):
+        sc = steps[k]["scores"]
+        a, b = int(order_ref[k]), int(order_ref[k + 1])
+        if sc[a] > 0 and sc[b] > 0:
+            r = sc[b] / sc[a]
+            if best is None or r < best[0]:
+                best = (r, k, a, b)
+    r, k, a, b = best
+    Dp = D.copy()
+    f = math.sqrt((1.0 - 3e-4) / r)
+    neg = Dp[b] < 0
+    Dp[b, neg] *= f
+    return Dp, k, a, b
+
+
+@pytest.mark.parametrize("name", ["pr1", "fmri"])
+def test_certified_order_repairs_a_planted_near_tie(vl, h, name):
+    """The search on a D whose step-k scores were moved by 3e-4 relative (a
+    near tie, as an FP32 measure can produce) takes the wrong variable; the
+    certified ordering re-decides that step on FP64 entries recomputed from
+    E, changes the pick and resumes: the result is the oracle's order."""
+    inst = synth.make_config(name)
+    ref = _ref_pipeline(name, inst)
+    od = oracle.order_heuristic(ref["D"])
+    Dp, k, a, b = _planted_near_tie(ref["D"], ref["order"], od["steps"])
+    plain = [int(c) for c in oracle.order_heuristic(Dp)["order"]]
+    assert plain[k] == b and plain != [int(c) for c in ref["order"]]
+    m = Dp.shape[0]
+    Dt = torch.from_numpy(Dp).cuda()
+    Et = torch.from_numpy(np.ascontiguousarray(ref["E"])).cuda()
+    o_plain = torch.empty(m, dtype=torch.int32, device="cuda")
+    vl.vl_causal_order(h, Dt, o_plain)
+    order = torch.empty(m, dtype=torch.int32, device="cuda")
+    stats = torch.zeros(4, dtype=torch.int32, device="cuda")
+    vl.vl_causal_order_certified(h, Dt, Et, order, None, stats)
+    h.sync()
+    assert [int(c) for c in o_plain.cpu().numpy()] == plain
+    st = [int(v) for v in stats.cpu().numpy()]
+    _report(f"planted near tie {name}", k=k, flagged=st[0], pairs=st[1], changed=st[2],
+            unverified=st[3])
+    assert [int(c) for c in order.cpu().numpy()] == [int(c) for c in ref["order"]], st
+    assert st[0] >= 1 and st[2] >= 1 and st[3] == 0, st
+
+
+def test_certified_fused_call_matches_steps(vl, h):
+    inst = synth.make_config("fmri")
+    X = torch.from_numpy(inst.X).cuda()
+    a = vl.fit(h, X, inst.p, prec="mixed_certified", steps=False)
+    b = vl.fit(h, X, inst.p, prec="mixed_certified", steps=True)
+    assert torch.equal(a["order"], b["order"])
+    assert (a["B0"] - b["B0"]).abs().max().item() <= 1e-6
+
+
+@pytest.mark.parametrize("seed,radius,w_lo,w_hi", [(13, 0.95, 0.5, 0.7), (14, 0.97, 0.6, 0.8),
+                                                   (11, 0.99, 0.8, 0.95)])
+def test_ill_conditioned_var_meets_tolerance_or_reports_rank(vl, h, seed, radius, w_lo, w_hi):
+    """VAR(3) systems whose centred lag Gram has condition numbers of about
+    1.5e5, 3e6 and 4e7 (companion radius near 1, strong instantaneous edges).
+    The mixed path factors the normal equations in FP32 and refines the
+    coefficients once with a double-float residual: it must either meet the
+    tolerances (B0 and B_tau within 1e-4 absolute; M within 1e-4 of max|M| --
+    the well-conditioned workloads hold M to 1e-5, an error that grows with
+    the condition number) or report VL_ERR_RANK (an FP32 pivot below 1e-6 of
+    its diagonal) -- never return a silently wrong fit."""
+    inst = synth.make_instance(60, 1500, 3, seed, "laplace", 0.3, w_lo, w_hi, "unif", radius)
+    M_ref, E_ref = oracle.var_ols(inst.X, 3)
+    X = torch.from_numpy(inst.X).cuda()
+    try:
+        out = vl.fit(h, X, 3, prec="mixed", steps=True)
+    except vl.VLError as e:
+        assert e.code == 3, e
+        _report(f"ill-conditioned VAR seed={seed}", rank_error=1)
+        return
+    M = out["M"].cpu().numpy()
+    m_err = np.abs(M - M_ref).max() / np.abs(M_ref).max()
+    order = out["order"].cpu().numpy()
+    B0_ref = oracle.b0_ols(E_ref, order)
+    b_err = np.abs(out["B0"].cpu().numpy() - B0_ref).max()
+    t_err = np.abs(out["Btau"].cpu().numpy() - oracle.btau(B0_ref, M_ref)).max()
+    _report(f"ill-conditioned VAR seed={seed}", m_err_rel=m_err, b0_err=b_err, btau_err=t_err)
+    assert m_err <= 1e-4 and b_err <= B_ABS and t_err <= B_ABS, (m_err, b_err, t_err)
