@@ -134,7 +134,8 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   const int nblk = (mp + CHOL_NB - 1) / CHOL_NB;
   const size_t part_cap =
       (size_t)16 * std::max((size_t)m * m, (size_t)mp * mp) +
-      (sizeof(T) == 4 ? (size_t)4 * m * (p + 1) * m * (p + 1) : 0);  // tensor-core split-K
+      (sizeof(T) == 4 ? (size_t)4 * m * (p + 1) * m * (p + 1) + (size_t)m * (n - p)
+                      : 0);  // tensor-core split-K and residual partials
   const bool tc = sizeof(T) == 4;  // mixed: the Gram on the tensor cores
   const int64_t kp = tg_kpad(n_eff), plane = (int64_t)q * kp;
   T *Xc, *Gzz, *Gzy, *dinv;
@@ -142,6 +143,8 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   char* S = nullptr;
   int* exps = nullptr;
   float *nhi = nullptr, *nlo = nullptr, *rr = nullptr;
+  char *St = nullptr, *Sb = nullptr;
+  int* aexp = nullptr;
   vl_status s = with_workspace(x, [&](Arena& a) {
     Xc = a.take<T>((size_t)m * ldc);
     mu = a.take<double>(m);
@@ -153,6 +156,9 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
       nhi = a.take<float>((size_t)mp * q);
       nlo = a.take<float>((size_t)mp * q);
       rr = a.take<float>((size_t)mp * m);
+      St = a.take<char>(3 * (size_t)n * tg_kpad(m) * 2);
+      Sb = a.take<char>(3 * (size_t)m * p * tg_kpad(m) * 2);
+      aexp = a.take<int>(m);
     } else {
       G = a.take<double>((size_t)mp * q);
     }
@@ -186,7 +192,11 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
       }
   }
   launch_var_normal_eq<T>(G, m, p, n_eff, wbar, Gzz, Gzy, st, nhi, nlo);
-  chol_blocked<T>(cx, Gzz, mp, mp, dinv, diag0);
+  // Mixed: the FP32 lag Gram is accurate to about FP32 rounding, so a lag
+  // variable explained by the earlier ones to within 1e-3 of its variance
+  // (relative pivot below 1e-3) leaves coefficients whose error exceeds the
+  // tolerances; the fit reports VL_ERR_RANK instead (VL_PREC_FP64 fits it).
+  chol_blocked<T>(cx, Gzz, mp, mp, dinv, diag0, sizeof(T) == 4 ? 1e-3 : -1.0);
   chol_solve_blocked<T>(cx, Gzz, mp, dinv, mp, Gzy, m, m, true);
   if constexpr (sizeof(T) == 4) {
     // one step of iterative refinement: r = G_zy - G_zz beta0 in
@@ -198,11 +208,17 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   } else {
     launch_var_coef<T>(Gzy, m, p, wbar, M, cst, st);
   }
-  launch_var_resid_init(X, ldx, m, n, p, mu, cst, E, n_eff, st);
-  for (int tau = 1; tau <= p; ++tau) {
-    View<T> A{Gzy + (int64_t)(tau - 1) * m * m, 1, m};  // A(i, k) = M_tau[i][k]
-    View<T> B{Xc + (p - tau), 1, ldc};                 // B(t, k) = Xc[k][p - tau + t]
-    launch_gemm<T, double>(cx, m, n_eff, m, -1.0, A, B, 1.0, E, n_eff, false);
+  if constexpr (sizeof(T) == 4) {
+    // residuals on the tensor cores (exact slices of beta and the series)
+    if (!launch_tc_var_resid(cx, Xc, ldc, X, ldx, m, n, p, Gzy, exps, mu, cst, St, Sb, aexp, E))
+      return fail(x.h, VL_ERR_CUDA, "vl_var_fit: tensor map encoding unavailable");
+  } else {
+    launch_var_resid_init(X, ldx, m, n, p, mu, cst, E, n_eff, st);
+    for (int tau = 1; tau <= p; ++tau) {
+      View<T> A{Gzy + (int64_t)(tau - 1) * m * m, 1, m};  // A(i, k) = M_tau[i][k]
+      View<T> B{Xc + (p - tau), 1, ldc};                 // B(t, k) = Xc[k][p - tau + t]
+      launch_gemm<T, double>(cx, m, n_eff, m, -1.0, A, B, 1.0, E, n_eff, false);
+    }
   }
   return check_launch(x.h, "vl_var_fit");
 }
@@ -973,6 +989,8 @@ vl_status vl_reserve(vl_handle h, int m, int n, int p) {
   // bf16 slices of W and of E) and the certified ordering's FP64 cache
   const size_t q = (size_t)m * (std::max(p, 1) + 1);
   b += 8 * 5 * q * q + 6 * (q + (size_t)m) * ln + 24 * mm;
+  // the residual product's slices and partials
+  b += 6 * ln * (mpad + 64) + 6 * mp * (mpad + 64) + 8 * (size_t)m * ln;
   DeviceGuard g(h->device);
   return ensure_ws(h, b);
 }

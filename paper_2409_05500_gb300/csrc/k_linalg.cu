@@ -867,9 +867,11 @@ void launch_gemm_split(const Ctx& cx, int M, int N, int K, View<float> Ahi, View
 }
 
 template <class T>
-void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag0) {
+void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag0,
+                  double pivot_floor) {
   const int NB = CHOL_NB;
   cudaStream_t s = cx.s;
+  const double rel_tol = pivot_floor > 0 ? pivot_floor : (sizeof(T) == 4 ? 1e-6 : 1e-12);
   if constexpr (sizeof(T) == 4) {
     if (n <= SINGLE_MAX) {
       const size_t smem1 = chol_single_smem(SINGLE_MAX);
@@ -881,10 +883,10 @@ void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag
       }
       note_launch();
       save_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
-      if (launch_chol_cluster(A, lda, n, dinv, diag0, 1e-6f, cx.st, s)) return;
+      if (launch_chol_cluster(A, lda, n, dinv, diag0, (float)rel_tol, cx.st, s)) return;
       note_launch();
-      chol_single_kernel<<<1, STH, chol_single_smem(n), s>>>(A, lda, n, dinv, diag0, 1e-6f,
-                                                            cx.st);
+      chol_single_kernel<<<1, STH, chol_single_smem(n), s>>>(A, lda, n, dinv, diag0,
+                                                            (float)rel_tol, cx.st);
       return;
     }
   }
@@ -895,7 +897,6 @@ void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag
                          (int)smem);
     attr_set = true;
   }
-  const double rel_tol = sizeof(T) == 4 ? 1e-6 : 1e-12;
   note_launch();
   save_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -917,8 +918,8 @@ void chol_blocked(const Ctx& cx, T* A, int64_t lda, int n, T* dinv, double* diag
                       A + (int64_t)(k0 + nb) * (lda + 1), lda, true);
   }
 }
-template void chol_blocked<float>(const Ctx&, float*, int64_t, int, float*, double*);
-template void chol_blocked<double>(const Ctx&, double*, int64_t, int, double*, double*);
+template void chol_blocked<float>(const Ctx&, float*, int64_t, int, float*, double*, double);
+template void chol_blocked<double>(const Ctx&, double*, int64_t, int, double*, double*, double);
 
 template <class T>
 void chol_solve_blocked(const Ctx& cx, const T* L, int64_t lda, const T* dinv, int n, T* R,

@@ -183,13 +183,91 @@ __global__ void slice_lags_kernel(const float* __restrict__ Xc, int64_t ldc, int
   }
 }
 
+// The VAR residual product (Sec. 4.1, E = Y - sum_tau M_tau Z_tau) as one
+// Gram-type product over K = (tau, k): A = beta' (m rows), B = the time-major
+// series (rows t).  The per-variable scale of the series moves into A, so
+// that every row of B shares one scale: A[i][(tau-1) mp + k] = M_tau[i][k]
+// 2^(e_k) and B[s][k] = Xc[k][s] 2^(-e_k), whose product is M_tau[i][k]
+// Xc[k][s] exactly.
+// Time-major slices of the normalised series: St[z][s][k], k < kp (zeros for
+// k >= m), from Xc (m rows, stride ldc) and the variables' exponents.
+__global__ void slice_time_kernel(const float* __restrict__ Xc, int64_t ldc, int m, int n,
+                                  int kp, const int* __restrict__ vexp,
+                                  __nv_bfloat16* __restrict__ St, int64_t plane) {
+  __shared__ float tile[32][33];
+  const int s0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, t = s0 + tx;
+    tile[r][tx] = (k < m && t < n) ? ldexpf(Xc[(int64_t)k * ldc + t], 7 - vexp[k]) : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int t = s0 + r, k = k0 + tx;
+    if (t >= n || k >= kp) continue;
+    __nv_bfloat16 a, b, c;
+    slice3(tile[tx][r], 0.f, a, b, c);
+    __nv_bfloat16* o = St + (int64_t)t * kp + k;
+    o[0] = a;
+    o[plane] = b;
+    o[2 * plane] = c;
+  }
+}
+
+// Slices of beta' (m rows, K = p kp): row i, column (tau-1) kp + k holds
+// beta[(tau-1) m + k][i] 2^(e_k) (zeros for k >= m), with the row exponent.
+__global__ void slice_beta_kernel(const float* __restrict__ beta, int m, int p, int kp,
+                                  const int* __restrict__ vexp, __nv_bfloat16* __restrict__ Sb,
+                                  int64_t plane, int* __restrict__ aexp) {
+  __shared__ unsigned long long red[32];
+  const int i = blockIdx.x, K = p * kp;
+  unsigned long long mx = 0;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const int tau = c / kp, k = c % kp;
+    if (k >= m) continue;
+    const float a = ldexpf(beta[((int64_t)tau * m + k) * m + i], vexp[k]);
+    const unsigned long long b = __float_as_uint(a) & 0x7fffffffu;
+    mx = b > mx ? b : mx;
+  }
+  const unsigned long long fb = block_max_u64(mx, red);
+  const int ex = fb == 0 ? 0 : clamp_exp((int)((fb >> 23) & 0xff) - 126);
+  if (threadIdx.x == 0) aexp[i] = ex;
+  __nv_bfloat16* o = Sb + (int64_t)i * K;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const int tau = c / kp, k = c % kp;
+    const float a = k < m ? ldexpf(beta[((int64_t)tau * m + k) * m + i], vexp[k] + 7 - ex) : 0.f;
+    __nv_bfloat16 s0, s1, s2;
+    slice3(a, 0.f, s0, s1, s2);
+    o[c] = s0;
+    o[plane + c] = s1;
+    o[2 * plane + c] = s2;
+  }
+}
+
+// E[i][t] = X[i][p + t] - (mu_i + cst_i) - 2^(a_i - 14) (product), t < n_eff.
+__global__ void resid_apply_kernel(const double* __restrict__ X, int64_t ldx, int m, int n_eff,
+                                   int p, const double* __restrict__ mu,
+                                   const double* __restrict__ cst, const float2* __restrict__ part,
+                                   const int* __restrict__ aexp, double* __restrict__ E) {
+  const int i = blockIdx.y;
+  const double off = mu[i] + cst[i];
+  const int ex = aexp[i] - 14;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_eff; t += gridDim.x * blockDim.x) {
+    const float2 v = part[(int64_t)i * n_eff + t];
+    E[(int64_t)i * n_eff + t] =
+        X[(int64_t)i * ldx + p + t] - off - ldexp((double)v.x + (double)v.y, ex);
+  }
+}
+
 // --------------------------------------------------------- the product
 struct TgParams {
   int M, N;            // output rows / columns
   int nkb;             // K-blocks (of 64) over the whole K
-  int kb_per_split;    // K-blocks per CTA (a multiple of TG_SEG except the last)
+  int kb_per_split;    // K-blocks per CTA (the last CTA may have fewer)
   int tiles_n;         // 64-wide column tiles
   int sym;             // 1: only tiles reaching the upper triangle (A == B)
+  int lag_kb;          // > 0: B is read as lag windows (see tcgram_kernel)
+  int lag_p;
   float2* part;        // [split][M][N] double-float partials
   int* st;             // sticky status word
 };
@@ -284,9 +362,18 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
         if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, abort_flag, WAIT_LIMIT)) break;
         tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
         unsigned char* st = smem + s * STAGE_BYTES;
-        const int kx = (kb0 + it) * TG_K;
+        const int kb = kb0 + it, kx = kb * TG_K;
         tc::tma_load_3d(st, &mapA, &full[s], kx, row0, 0);
-        tc::tma_load_3d(st + TG_SL * A_SLICE, &mapB, &full[s], kx, col0, 0);
+        if (P.lag_kb > 0) {
+          // K-block kb belongs to lag tau = kb / lag_kb + 1: rows t of B are
+          // the time-major slices at time p - tau + t (a row offset: no
+          // alignment rule), columns the variables of that K-block
+          const int tau = kb / P.lag_kb + 1;
+          tc::tma_load_3d(st + TG_SL * A_SLICE, &mapB, &full[s], (kb % P.lag_kb) * TG_K,
+                          col0 + P.lag_p - tau, 0);
+        } else {
+          tc::tma_load_3d(st + TG_SL * A_SLICE, &mapB, &full[s], kx, col0, 0);
+        }
         ++issued;
       }
       if (issued < nkb) *abort_flag = 1;
@@ -523,8 +610,7 @@ bool launch_tcgram_sym(const Ctx& cx, const void* S, int N, int Kpad, int64_t ld
   int splits = std::max(1, std::min(nseg, cx.num_sms / std::max(1, tiles)));
   const size_t per = (size_t)N * N;
   splits = (int)std::max<size_t>(1, std::min<size_t>(splits, cx.part_cap / per));
-  const int segs_per = (nseg + splits - 1) / splits;
-  P.kb_per_split = segs_per * TG_SEG;
+  P.kb_per_split = (P.nkb + splits - 1) / splits;  // a CTA forms its own segments
   splits = (P.nkb + P.kb_per_split - 1) / P.kb_per_split;
   P.part = reinterpret_cast<float2*>(cx.part);
   P.st = cx.st;
@@ -533,6 +619,57 @@ bool launch_tcgram_sym(const Ctx& cx, const void* S, int N, int Kpad, int64_t ld
   note_launch();
   tg_reduce_sym_kernel<<<(unsigned)((per + 255) / 256), 256, 0, cx.s>>>(P.part, splits, N, exps,
                                                                        C, ldc);
+  return true;
+}
+
+// The VAR residuals on the tensor cores: E = X[:, p:] - mu - cst - sum_tau
+// M_tau Z_tau with beta (FP32, mp x m) and the centred FP32 series Xc;
+// vexp: the variables' exponents (those of the lag slicing).  Scratch: St
+// (3 n kp bf16), Sb (3 m p kp bf16), aexp (m ints); the partials in the
+// context's split-K buffer (m n_eff float2).  kp = tg_kpad(m).
+bool launch_tc_var_resid(const Ctx& cx, const float* Xc, int64_t ldc, const double* X,
+                         int64_t ldx, int m, int n, int p, const float* beta, const int* vexp,
+                         const double* mu, const double* cst, void* St, void* Sb, int* aexp,
+                         double* E) {
+  const int kp = (int)tg_kpad(m), n_eff = n - p, K = p * kp;
+  const int64_t plane_t = (int64_t)n * kp, plane_b = (int64_t)m * K;
+  if ((size_t)m * n_eff > cx.part_cap) return false;
+  note_launch();
+  slice_time_kernel<<<dim3((n + 31) / 32, kp / 32), dim3(32, 8), 0, cx.s>>>(
+      Xc, ldc, m, n, kp, vexp, static_cast<__nv_bfloat16*>(St), plane_t);
+  note_launch();
+  slice_beta_kernel<<<m, 256, 0, cx.s>>>(beta, m, p, kp, vexp, static_cast<__nv_bfloat16*>(Sb),
+                                          plane_b, aexp);
+  CUtensorMap mA, mB;
+  if (!make_slice_map(&mA, Sb, K, m, K, plane_b, TG_M) ||
+      !make_slice_map(&mB, St, kp, n, kp, plane_t, TG_N))
+    return false;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tcgram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TG_SMEM) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  TgParams P{};
+  P.M = m;
+  P.N = n_eff;
+  P.sym = 0;
+  P.tiles_n = (n_eff + TG_N - 1) / TG_N;
+  const int tiles = ((m + TG_M - 1) / TG_M) * P.tiles_n;
+  P.nkb = K / TG_K;
+  P.kb_per_split = P.nkb;  // one split: the tiles fill the GPU
+  P.lag_kb = kp / TG_K;
+  P.lag_p = p;
+  P.part = reinterpret_cast<float2*>(cx.part);
+  P.st = cx.st;
+  note_launch();
+  tcgram_kernel<<<dim3(tiles, 1), TG_THREADS, TG_SMEM, cx.s>>>(mA, mB, P);
+  note_launch();
+  resid_apply_kernel<<<dim3((n_eff + 255) / 256 < 16 ? (n_eff + 255) / 256 : 16, m), 256, 0,
+                       cx.s>>>(X, ldx, m, n_eff, p, mu, cst, P.part, aexp, E);
   return true;
 }
 

@@ -173,8 +173,8 @@ size_t gemm_part_need(int M, int N, int K);
 // Cholesky of the n x n SPD matrix A (T, row-major, lda, lower part used) in
 // place; the inverse of every nb x nb diagonal block of L is written to
 // dinv (T, ceil(n/nb) blocks of nb*nb).  diag0 (n doubles) receives the
-// original diagonal; a pivot below 1e-6 (FP32) / 1e-12 (FP64) of it sets
-// VL_ERR_RANK.
+// original diagonal; a pivot below 1e-6 (FP32) / 1e-12 (FP64) of it (or
+// below pivot_floor of it) sets VL_ERR_RANK.
 // Triangular solves with the solution panel in shared memory (n <= 1024);
 // false if not launched (the caller then uses trsm_cols_kernel).
 template <class T>
@@ -186,7 +186,9 @@ bool launch_chol_cluster(float* A, int64_t lda, int n, float* dinv, const double
                          float rel_tol, int* st, cudaStream_t s,
                          unsigned long long* prof = nullptr);
 template <class T>
-void chol_blocked(const Ctx& c, T* A, int64_t lda, int n, T* dinv, double* diag0);
+// pivot_floor > 0 replaces the default relative pivot floor.
+void chol_blocked(const Ctx& c, T* A, int64_t lda, int n, T* dinv, double* diag0,
+                  double pivot_floor = -1.0);
 // Solve L Y = R (forward) then optionally L^T X = Y (backward) for nrhs
 // right-hand sides held in R (n x nrhs, row-major, ldr), in place.
 template <class T>
@@ -258,6 +260,14 @@ void launch_slice_lags(const float* Xc, int64_t ldc, int m, int n, int p, int64_
                        int64_t plane, int* exps, cudaStream_t s);
 bool launch_tcgram_sym(const Ctx& cx, const void* S, int N, int Kpad, int64_t ldo, int64_t plane,
                        const int* exps, double* C, int64_t ldc);
+// The VAR residuals E = X[:, p:] - mu - cst - sum_tau M_tau Z_tau as one
+// tensor-core product (beta: FP32 mp x m; vexp: the variables' slice
+// exponents of launch_slice_lags); false if the tensor maps cannot be made or
+// the split-K buffer is smaller than m (n - p).
+bool launch_tc_var_resid(const Ctx& cx, const float* Xc, int64_t ldc, const double* X,
+                         int64_t ldx, int m, int n, int p, const float* beta, const int* vexp,
+                         const double* mu, const double* cst, void* St, void* Sb, int* aexp,
+                         double* E);
 
 // Certified ordering (k_certify.cu): after a search on an FP32-measure D
 // (launch_causal_order with spick = certify_spick(cert_ws, m)), near ties
