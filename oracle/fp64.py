@@ -277,7 +277,8 @@ def order_gap_ok(order_gpu: Sequence[int], D_ref: np.ndarray, rel_gap: float = 1
 
 
 def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: float = 1e-6,
-                          d_tol: float = 0.0, gaps_cand: Optional[Sequence[float]] = None
+                          d_tol: float = 0.0, gaps_cand: Optional[Sequence[float]] = None,
+                          only_steps: Optional[Sequence[int]] = None
                           ) -> Tuple[bool, int, List[int]]:
     """Order comparison rule for the iterative search of Section 3: the
     search of :func:`order_standard` is replayed, but every iteration removes
@@ -296,11 +297,16 @@ def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: fl
     moves by more than B (the largest band above), neither do the two
     smallest, and the gap moves by at most 2 B / (S_(2) - B), plus rel_gap.
 
+    With only_steps, the measure is evaluated (and the step checked) only at
+    those iterations; the others just apply Eq. 4 on the candidate's pick, so
+    that a long search can be checked on a sample of its iterations.
+
     Returns (ok, number of near-tie steps, list of failing steps)."""
     X = np.array(Xs, dtype=np.float64, copy=True)
     m = X.shape[0]
     if sorted(int(c) for c in order_cand) != list(range(m)):
         return False, 0, [-1]
+    check = None if only_steps is None else set(int(k) for k in only_steps)
     U = list(range(m))
     ties = 0
     bad: List[int] = []
@@ -308,6 +314,11 @@ def order_standard_gap_ok(Xs: np.ndarray, order_cand: Sequence[int], rel_gap: fl
         c = int(c)
         if len(U) == 1:
             break
+        if check is not None and k not in check:
+            U.remove(c)
+            for j in U:  # Eq. 4 on the candidate's pick
+                X[j] = residual(X[j], X[c])
+            continue
         D = pairwise_measure(standardize(X[U]))["D"]
         loc = {v: a for a, v in enumerate(U)}
         sub = scores_over(D, range(len(U)))

@@ -254,3 +254,20 @@ def test_heuristic_accuracy_close_to_the_iterative_search():
     r = np.array(rows).mean(axis=0)
     assert r[2] >= 0.95 and r[3] >= 0.95
     assert abs(r[1] - r[0]) <= 0.1
+
+
+def test_standard_gap_check_on_sampled_steps_agrees_with_the_full_check():
+    """Checking the iterative search on a sample of its iterations (the other
+    iterations only refine the data, Eq. 4) accepts the oracle's own order and
+    rejects a wrong pick at a sampled iteration, like the full check."""
+    inst = synth.make_instance(7, 2000, 1, 77, "uniform", 0.4, 0.3, 0.8, "unif", 0.3)
+    M, E = oracle.var_ols(inst.X, 1)
+    Xs = oracle.standardize(E)
+    order = [int(c) for c in oracle.order_standard(Xs)["order"]]
+    assert oracle.order_standard_gap_ok(Xs, order)[0]
+    assert oracle.order_standard_gap_ok(Xs, order, only_steps=[0, 3, 5])[0]
+    wrong = order[:3] + [order[4], order[3]] + order[5:]
+    full = oracle.order_standard_gap_ok(Xs, wrong)
+    sampled = oracle.order_standard_gap_ok(Xs, wrong, only_steps=[3])
+    assert not full[0] and 3 in full[2]
+    assert not sampled[0] and sampled[2] == [3]
