@@ -143,6 +143,7 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   char* S = nullptr;
   int* exps = nullptr;
   float *nhi = nullptr, *nlo = nullptr, *rr = nullptr;
+  float2* rpart = nullptr;
   char *St = nullptr, *Sb = nullptr;
   int* aexp = nullptr;
   vl_status s = with_workspace(x, [&](Arena& a) {
@@ -156,6 +157,7 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
       nhi = a.take<float>((size_t)mp * q);
       nlo = a.take<float>((size_t)mp * q);
       rr = a.take<float>((size_t)mp * m);
+      rpart = a.take<float2>((size_t)refine_splits(m, p, x.h->num_sms) * mp * m);
       St = a.take<char>(3 * (size_t)n * tg_kpad(m) * 2);
       Sb = a.take<char>(3 * (size_t)m * p * tg_kpad(m) * 2);
       aexp = a.take<int>(m);
@@ -201,7 +203,7 @@ vl_status var_fit_impl(Exec& x, const double* X, int64_t ldx, int m, int n, int 
   if constexpr (sizeof(T) == 4) {
     // one step of iterative refinement: r = G_zy - G_zz beta0 in
     // double-float, the correction from the same FP32 factor
-    launch_refine_residual(nhi, nlo, m, p, Gzy, rr, st);
+    launch_refine_residual(nhi, nlo, m, p, Gzy, rr, rpart, cx.num_sms, st);
     chol_solve_blocked<T>(cx, Gzz, mp, dinv, mp, rr, m, m, true);
     launch_refine_apply(Gzy, rr, m, p, M, st);
     launch_var_cst<T>(Gzy, m, p, wbar, cst, st);

@@ -12,6 +12,8 @@
 // with the normal equations split into FP32 (hi, lo) pairs and every product
 // and sum kept as an exact or compensated double-float (about 2^-44
 // relative), so only beta's own rounding and the Gram's error remain.
+#include <algorithm>
+
 #include "vl_internal.cuh"
 
 namespace vl {
@@ -24,14 +26,16 @@ constexpr int RTH = 128; // threads: 8 x 16, each 4 rows x 2 columns (one float2
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// r[a][i] = NE[a][i] - sum_c NE[a][m + c] beta0[c][i], a < mp, i < m, with
-// NE = (hi + lo) the centred normal equations (mp x q, q = m (p + 1)) and
-// beta0 (FP32, mp x m), with double-float accumulators (the two columns of a
-// thread as one float2, on the paired FP32 instructions); r rounded to FP32
-// at the end (it is small, and only feeds the FP32 correction solve).
-__global__ void __launch_bounds__(RTH, 2)
+// Partial sums sum_{c in split z} NE[a][m + c] beta0[c][i], a < mp, i < m,
+// with NE = (hi + lo) the centred normal equations (mp x q, q = m (p + 1))
+// and beta0 (FP32, mp x m), as double-float pairs (the two columns of a
+// thread as one float2, on the paired FP32 instructions).  The K range (c) is
+// split over blockIdx.z in chunks of kchunk so that the grid fills the GPU;
+// part[z][a][i] = (hi, lo) of split z.
+__global__ void __launch_bounds__(RTH, 4)
     refine_residual_kernel(const float* __restrict__ nhi, const float* __restrict__ nlo, int m,
-                           int mp, const float* __restrict__ beta0, float* __restrict__ r) {
+                           int mp, const float* __restrict__ beta0, int kchunk,
+                           float2* __restrict__ part) {
   __shared__ float Ah[RK][RT + 1], Al[RK][RT + 1];
   __shared__ __align__(8) float Bs[RK][RT];
   const int q = m + mp;
@@ -41,16 +45,17 @@ __global__ void __launch_bounds__(RTH, 2)
   float2 sh[4], sl[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) sh[u] = sl[u] = f2(0.f, 0.f);
-  for (int c0 = 0; c0 < mp; c0 += RK) {
+  const int cbeg = blockIdx.z * kchunk, cend = min(mp, cbeg + kchunk);
+  for (int c0 = cbeg; c0 < cend; c0 += RK) {
     for (int idx = threadIdx.x; idx < RK * RT; idx += RTH) {
       const int kk = idx % RK, rr = idx / RK;  // A: rows a, consecutive k per thread group
       const int a = a0 + rr, c = c0 + kk;
-      const bool ok = a < mp && c < mp;
+      const bool ok = a < mp && c < cend;
       Ah[kk][rr] = ok ? nhi[(int64_t)a * q + m + c] : 0.f;
       Al[kk][rr] = ok ? nlo[(int64_t)a * q + m + c] : 0.f;
       const int kb = idx / RT, ii = idx % RT;  // B: rows c, consecutive i
       const int cb = c0 + kb, i = i0 + ii;
-      Bs[kb][ii] = (cb < mp && i < m) ? beta0[(int64_t)cb * m + i] : 0.f;
+      Bs[kb][ii] = (cb < cend && i < m) ? beta0[(int64_t)cb * m + i] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -81,15 +86,38 @@ __global__ void __launch_bounds__(RTH, 2)
     for (int v = 0; v < 2; ++v) {
       const int i = i0 + tx * 2 + v;
       if (i >= m) continue;
-      const float h = v ? sh[u].y : sh[u].x, l = v ? sl[u].y : sl[u].x;
-      // r = (yh + yl) - (h + l)
-      const float yh = nhi[(int64_t)a * q + i], yl = nlo[(int64_t)a * q + i];
-      const float d = yh - h;
-      const float bp = d - yh;
-      const float err = (yh - (d - bp)) + (-h - bp);
-      r[(int64_t)a * m + i] = d + (err + (yl - l));
+      part[((int64_t)blockIdx.z * mp + a) * m + i] =
+          v ? make_float2(sh[u].y, sl[u].y) : make_float2(sh[u].x, sl[u].x);
     }
   }
+}
+
+// r[a][i] = NE[a][i] - sum_z part[z][a][i]: the split partials added in
+// double-float (TwoSum), the difference with the right-hand side likewise;
+// r rounded to FP32 at the end (it is small, and only feeds the FP32
+// correction solve).
+__global__ void refine_reduce_kernel(const float* __restrict__ nhi, const float* __restrict__ nlo,
+                                     int m, int mp, const float2* __restrict__ part, int splits,
+                                     float* __restrict__ r) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)mp * m) return;
+  const int a = (int)(idx / m), i = (int)(idx % m);
+  float h = 0.f, l = 0.f;
+  for (int z = 0; z < splits; ++z) {
+    const float2 v = part[(int64_t)z * mp * m + idx];
+    const float s = h + v.x;
+    const float bp = s - h;
+    const float err = (h - (s - bp)) + (v.x - bp);
+    h = s;
+    l += err + v.y;
+  }
+  // r = (yh + yl) - (h + l)
+  const int q = m + mp;
+  const float yh = nhi[(int64_t)a * q + i], yl = nlo[(int64_t)a * q + i];
+  const float d = yh - h;
+  const float bp = d - yh;
+  const float err = (yh - (d - bp)) + (-h - bp);
+  r[idx] = d + (err + (yl - l));
 }
 
 // beta = beta0 + delta: M[tau][i][k] in FP64 from beta[(tau-1) m + k][i], and
@@ -107,12 +135,25 @@ __global__ void refine_apply_kernel(float* __restrict__ beta, const float* __res
 
 }  // namespace
 
-void launch_refine_residual(const float* nhi, const float* nlo, int m, int p, const float* beta0,
-                            float* r, cudaStream_t s) {
+int refine_splits(int m, int p, int num_sms) {
   const int mp = m * p;
-  dim3 grid((m + RT - 1) / RT, (mp + RT - 1) / RT);
+  const int base = ((m + RT - 1) / RT) * ((mp + RT - 1) / RT);
+  // about four CTAs per SM, each K chunk at least two staging rounds
+  return std::max(1, std::min({REFINE_MAX_SPLITS, (4 * num_sms + base - 1) / base,
+                               (mp + 2 * RK - 1) / (2 * RK)}));
+}
+
+void launch_refine_residual(const float* nhi, const float* nlo, int m, int p, const float* beta0,
+                            float* r, float2* part, int num_sms, cudaStream_t s) {
+  const int mp = m * p, splits = refine_splits(m, p, num_sms);
+  const int kchunk = ((mp + splits - 1) / splits + RK - 1) / RK * RK;
+  const int nz = (mp + kchunk - 1) / kchunk;
+  dim3 grid((m + RT - 1) / RT, (mp + RT - 1) / RT, nz);
   note_launch();
-  refine_residual_kernel<<<grid, RTH, 0, s>>>(nhi, nlo, m, mp, beta0, r);
+  refine_residual_kernel<<<grid, RTH, 0, s>>>(nhi, nlo, m, mp, beta0, kchunk, part);
+  const int64_t tot = (int64_t)mp * m;
+  note_launch();
+  refine_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nhi, nlo, m, mp, part, nz, r);
 }
 
 void launch_refine_apply(float* beta, const float* delta, int m, int p, double* M,

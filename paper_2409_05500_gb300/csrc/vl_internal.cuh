@@ -136,8 +136,13 @@ void launch_var_cst(const T* beta, int m, int p, const double* wbar, double* cst
 // One refinement step of the VAR coefficients (k_refine.cu): r = G_zy -
 // G_zz beta0 in double-float from the FP32 pairs (nhi, nlo); after the FP32
 // correction solve, beta = beta0 + delta into M (FP64) and beta0 (FP32).
+// The refinement residual's K range is split over up to REFINE_MAX_SPLITS
+// CTAs per output tile (refine_splits(m, p, num_sms) of them); part holds
+// that many m p x m blocks of float2 partial sums.
+constexpr int REFINE_MAX_SPLITS = 8;
+int refine_splits(int m, int p, int num_sms);
 void launch_refine_residual(const float* nhi, const float* nlo, int m, int p, const float* beta0,
-                            float* r, cudaStream_t s);
+                            float* r, float2* part, int num_sms, cudaStream_t s);
 void launch_refine_apply(float* beta, const float* delta, int m, int p, double* M,
                          cudaStream_t s);
 void launch_var_resid_init(const double* X, int64_t ldx, int m, int n, int p, const double* mu,
