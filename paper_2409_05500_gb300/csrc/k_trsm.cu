@@ -3,10 +3,14 @@
 // request, backward X = L^{-T} Y, for the VAR normal equations (Sec. 4.1) and
 // for L^{-1} itself, which gives B0 (Sec. 4.2 item 5).
 //
-// GB300 design.  Each CTA owns 4 right-hand-side columns (one per thread of a
-// row; 100 CTAs for 400 columns) and keeps its whole solution panel (n x 4) in
-// shared memory, so a block row never waits for its own earlier results to
-// come back from memory.  The 64 x 64 pieces of L (and
+// GB300 design.  Each CTA owns 4 right-hand-side columns (100 CTAs for 400
+// columns) and keeps its whole solution panel (n x 4) in shared memory, so a
+// block row never waits for its own earlier results to come back from memory.
+// A thread computes one row of the block row for all four columns over a
+// 16-wide slice of each piece (vector loads of the piece's row and of the
+// solution rows): a piece costs about 20 shared-memory loads per thread, not
+// 128, which is what limited the scalar one-column-per-thread form; the four
+// slices are added once per block row.  The 64 x 64 pieces of L (and
 // the diagonal-block inverses) flow through an NS-stage cp.async ring in one
 // stream over both passes, so the next pieces are in flight while the current
 // one is applied: the solve is paced by the L2 bandwidth of the pieces rather
@@ -51,6 +55,23 @@ __device__ __forceinline__ void wait_groups() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// Four consecutive elements from shared memory (16-byte aligned for float,
+// two 16-byte loads for double).
+template <class T>
+struct V4 {
+  T v[4];
+};
+__device__ __forceinline__ V4<float> ld_v4(const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld_v4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // Position in the piece stream: pass 0 (forward) then pass 1 (backward);
 // block rows in solve order; per block row its off-diagonal pieces, then the
 // inverse of its diagonal block (c == pieces(b)).
@@ -82,9 +103,9 @@ __global__ void __launch_bounds__(TTH) trsm_ring_kernel(const T* __restrict__ L,
   extern __shared__ __align__(16) unsigned char trsm_ring_smem[];
   const int nblk = (n + TB - 1) / TB;
   T* ring = reinterpret_cast<T*>(trsm_ring_smem);  // [NS][TB][LS]
-  T* Acc = ring + NS * TB * LS;                     // [TB][TSC]
-  T* Ysol = Acc + TB * TSC;                         // [nblk * TB][TSC]
-  const int tid = threadIdx.x, r = tid >> 2, cc = tid & 3;
+  T* Acc = ring + NS * TB * LS;                     // [TB][TSC], then [4][TB][TSC] slices
+  T* Ysol = Acc + 5 * TB * TSC;                     // [nblk * TB][TSC]
+  const int tid = threadIdx.x;
   const int c0 = blockIdx.x * TSC;
 
   // this CTA's columns of the right-hand side (zero beyond n and nrhs)
@@ -144,7 +165,14 @@ __global__ void __launch_bounds__(TTH) trsm_ring_kernel(const T* __restrict__ L,
     }
     commit();
   }
-  T acc = T(0);
+  // Thread (rr = tid % 64, ks = tid / 64): row rr of the block row, all TSC
+  // right-hand sides, over the k-slice [16 ks, 16 ks + 16) of every piece;
+  // the four slices are added once per block row, at its diagonal piece.
+  const int rr = tid & (TB - 1), ks = tid >> 6;
+  constexpr int KS = TB / 4;  // k-slice length
+  T part[TSC];
+#pragma unroll
+  for (int c = 0; c < TSC; ++c) part[c] = T(0);
   for (int i = 0; i < total; ++i) {
     wait_groups<NS - 2>();
     __syncthreads();
@@ -155,32 +183,81 @@ __global__ void __launch_bounds__(TTH) trsm_ring_kernel(const T* __restrict__ L,
     commit();
     const T* S = ring + (i % NS) * TB * LS;
     const int b = qc.block(nblk), k0 = b * TB, nb = min(TB, n - k0);
-    if (qc.c == 0) acc = Ysol[(k0 + r) * TSC + cc];  // start of a block row
     if (qc.c < qc.pieces(nblk)) {
       const int j0 = (qc.pass == 0 ? qc.c : b + 1 + qc.c) * TB;
-      const T* Y = Ysol + j0 * TSC + cc;
-      // four independent partial sums: the dot product is not one long chain
-      T a[4] = {T(0), T(0), T(0), T(0)};
-      if (qc.pass == 0) {
-#pragma unroll 16
-        for (int jj = 0; jj < TB; ++jj) a[jj & 3] += S[r * LS + jj] * Y[jj * TSC];
-      } else {
-#pragma unroll 16
-        for (int jj = 0; jj < TB; ++jj) a[jj & 3] += S[jj * LS + r] * Y[jj * TSC];
+      const T* Y = Ysol + (j0 + KS * ks) * TSC;
+      if (qc.pass == 0) {  // S[rr][jj]: row rr, four consecutive jj per vector load
+#pragma unroll
+        for (int j4 = 0; j4 < KS; j4 += 4) {
+          const V4<T> sv = ld_v4(S + rr * LS + KS * ks + j4);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const V4<T> y = ld_v4(Y + (j4 + e) * TSC);
+#pragma unroll
+            for (int c = 0; c < TSC; ++c) part[c] = fma_t(sv.v[e], y.v[c], part[c]);
+          }
+        }
+      } else {  // S[jj][rr] (the piece used transposed): consecutive rr across lanes
+#pragma unroll
+        for (int jj = 0; jj < KS; ++jj) {
+          const T sv = S[(KS * ks + jj) * LS + rr];
+          const V4<T> y = ld_v4(Y + jj * TSC);
+#pragma unroll
+          for (int c = 0; c < TSC; ++c) part[c] = fma_t(sv, y.v[c], part[c]);
+        }
       }
-      acc -= (a[0] + a[1]) + (a[2] + a[3]);
-    } else {  // apply the inverse of the diagonal block (transposed when backward)
-      Acc[r * TSC + cc] = acc;
+    } else {
+      // end of the block row: Acc = R - (the four slices' sums), then the
+      // inverse of the diagonal block (transposed when backward), again in
+      // four k-slices added through shared memory
+      T* red = Acc + TB * TSC;  // [4][TB][TSC]
+#pragma unroll
+      for (int c = 0; c < TSC; ++c) red[(ks * TB + rr) * TSC + c] = part[c];
       __syncthreads();
-      T o[4] = {T(0), T(0), T(0), T(0)};
-      if (qc.pass == 0) {
-#pragma unroll 16
-        for (int q = 0; q < TB; ++q) o[q & 3] += S[r * LS + q] * Acc[q * TSC + cc];
-      } else {
-#pragma unroll 16
-        for (int q = 0; q < TB; ++q) o[q & 3] += S[q * LS + r] * Acc[q * TSC + cc];
+      {
+        const int r2 = tid >> 2, c2 = tid & 3;  // one (row, column) per thread
+        T sum = Ysol[(k0 + r2) * TSC + c2];
+#pragma unroll
+        for (int z = 0; z < 4; ++z) sum -= red[(z * TB + r2) * TSC + c2];
+        Acc[r2 * TSC + c2] = sum;
       }
-      Ysol[(k0 + r) * TSC + cc] = r < nb ? (o[0] + o[1]) + (o[2] + o[3]) : T(0);
+      __syncthreads();
+      T o[TSC];
+#pragma unroll
+      for (int c = 0; c < TSC; ++c) o[c] = T(0);
+      const T* A = Acc + KS * ks * TSC;
+      if (qc.pass == 0) {
+#pragma unroll
+        for (int q4 = 0; q4 < KS; q4 += 4) {
+          const V4<T> sv = ld_v4(S + rr * LS + KS * ks + q4);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const V4<T> a = ld_v4(A + (q4 + e) * TSC);
+#pragma unroll
+            for (int c = 0; c < TSC; ++c) o[c] = fma_t(sv.v[e], a.v[c], o[c]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < KS; ++q) {
+          const T sv = S[(KS * ks + q) * LS + rr];
+          const V4<T> a = ld_v4(A + q * TSC);
+#pragma unroll
+          for (int c = 0; c < TSC; ++c) o[c] = fma_t(sv, a.v[c], o[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < TSC; ++c) red[(ks * TB + rr) * TSC + c] = o[c];
+      __syncthreads();
+      {
+        const int r2 = tid >> 2, c2 = tid & 3;
+        T sum = T(0);
+#pragma unroll
+        for (int z = 0; z < 4; ++z) sum += red[(z * TB + r2) * TSC + c2];
+        Ysol[(k0 + r2) * TSC + c2] = r2 < nb ? sum : T(0);
+      }
+#pragma unroll
+      for (int c = 0; c < TSC; ++c) part[c] = T(0);
     }
     qc.advance(nblk);
   }
@@ -195,7 +272,8 @@ __global__ void __launch_bounds__(TTH) trsm_ring_kernel(const T* __restrict__ L,
 template <class T>
 size_t ring_smem(int n) {
   const int nblk = (n + TB - 1) / TB;
-  return sizeof(T) * ((size_t)Ring<T>::NS * TB * Ring<T>::LS + TB * TSC + (size_t)nblk * TB * TSC);
+  return sizeof(T) *
+         ((size_t)Ring<T>::NS * TB * Ring<T>::LS + 5 * TB * TSC + (size_t)nblk * TB * TSC);
 }
 
 }  // namespace
