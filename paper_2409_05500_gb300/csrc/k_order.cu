@@ -105,6 +105,102 @@ __global__ void __launch_bounds__(OTH) order_kernel(const float* __restrict__ pt
   });
 }
 
+// The same search with P held in distributed shared memory: a cluster of
+// OC_CTAS CTAs, CTA t keeping the rows i in [t R, (t+1) R) of P for every
+// column c (R = ceil(m / OC_CTAS), layout [c][i - t R] as (hi, lo) pairs).  CTA 0
+// runs the search; the others only hold their rows until it is done.  A
+// step's load of P_{i,c} is then a distributed-shared-memory load (about 200
+// clocks) instead of an L2 load of Pt (about 750 clocks on this part, two
+// thirds of a step at m = 400).  The only synchronisation is a cluster barrier
+// after the rows are loaded and one at the end, so no CTA leaves while its
+// rows can still be read.
+constexpr int OC_CTAS = 8;
+constexpr int OC_MAX_M = 448;  // R m (hi, lo) pairs must fit one CTA's shared memory
+
+inline size_t oc_smem(int m) {
+  const int R = (m + OC_CTAS - 1) / OC_CTAS;
+  return (size_t)R * m * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(OTH) order_cluster_kernel(const float* __restrict__ pth,
+                                                            const float* __restrict__ ptl,
+                                                            const float* __restrict__ sh0,
+                                                            const float* __restrict__ sl0, int m,
+                                                            int32_t* __restrict__ order,
+                                                            double* __restrict__ spick) {
+  extern __shared__ __align__(16) float2 oc_rows[];
+  unsigned rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int R = (m + OC_CTAS - 1) / OC_CTAS;
+  const int i0 = (int)rank * R;
+  for (int idx = threadIdx.x; idx < R * m; idx += blockDim.x) {
+    const int c = idx / R, il = idx - c * R, i = i0 + il;
+    oc_rows[idx] = i < m ? make_float2(pth[(int64_t)c * m + i], ptl[(int64_t)c * m + i])
+                         : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  if (rank == 0) {
+    const int i = threadIdx.x;
+    float hi[1], lo[1];
+    bool alive[1];
+    alive[0] = i < m;
+    hi[0] = alive[0] ? sh0[i] : 0.f;
+    lo[0] = alive[0] ? sl0[i] : 0.f;
+    // this thread's row: owner CTA and local index, as a shared::cluster base
+    const int own = min(i / R, OC_CTAS - 1);
+    uint32_t base = (uint32_t)__cvta_generic_to_shared(oc_rows) + 8u * (uint32_t)(i - own * R);
+    asm volatile("mapa.shared::cluster.u32 %0, %0, %1;" : "+r"(base) : "r"(own));
+    const uint32_t stride = 8u * (uint32_t)R;
+    search_steps<1>(hi, lo, alive, m, 0, -1, order, spick, nullptr,
+                    [&](int c, int, float& h, float& l) {
+      asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];"
+                   : "=f"(h), "=f"(l)
+                   : "r"(base + stride * (uint32_t)c)
+                   : "memory");
+    });
+  }
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Launch the cluster search; false if m is out of its range or the cluster
+// cannot be launched (the caller then runs order_kernel).
+bool launch_order_cluster(const OrderWs& w, int m, int32_t* order, double* spick,
+                          cudaStream_t s) {
+  if (m < 64 || m > OC_MAX_M) return false;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(order_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)oc_smem(OC_MAX_M)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(OC_CTAS, 1, 1);
+  cfg.blockDim = dim3((m + 31) / 32 * 32, 1, 1);
+  cfg.dynamicSmemBytes = oc_smem(m);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = OC_CTAS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  note_launch();
+  if (cudaLaunchKernelEx(&cfg, order_cluster_kernel, (const float*)w.pth, (const float*)w.ptl,
+                         (const float*)w.sh, (const float*)w.sl, m, order, spick) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 // Gaps after the search, from the order: variable i replays its score
 // S_i = sum_{j in U} P_ij step by step in FP64; at the step that picks it, it
 // records its score as the minimum s1[k]; at earlier steps it offers its
@@ -187,6 +283,11 @@ void launch_causal_order(const double* D, int m, void* ws, int32_t* order, doubl
   pt_kernel<<<grid, block, 0, s>>>(D, m, w.pth, w.ptl, st);
   note_launch();
   rowsum_kernel<<<(m + 7) / 8, 256, 0, s>>>(D, m, w.sh, w.sl);
+  // P in distributed shared memory (64 <= m <= 448), unless profiling
+  if (!prof && launch_order_cluster(w, m, order, spick, s)) {
+    if (gap) launch_order_gaps(ws, m, order, gap, s);
+    return;
+  }
   // variables per thread: PER = 1 up to 1024 variables, then 2 and 4
   const int per = m <= OTH ? 1 : (m <= 2 * OTH ? 2 : 4);
   const int nthr = std::min(OTH, ((m + per - 1) / per + 31) / 32 * 32);
