@@ -10,7 +10,8 @@
 // CTA t owns row blocks R_b with b = t (mod cl), columns 0 .. 32(b+1)-1.
 // Step k (block column C_k):
 //   - the owner of R_k has factored the diagonal block A[R_k][C_k] and
-//     inverted it (one warp, registers and shared-memory broadcasts);
+//     inverted it (two warps: one factors, the other builds the inverse one
+//     column behind);
 //   - every CTA copies that 32 x 32 inverse out of the owner's shared memory
 //     (distributed shared memory) and forms the panel rows of its own row
 //     blocks, L[R_b][C_k] = A[R_b][C_k] Linv^T, in place;
@@ -115,91 +116,93 @@ inline size_t cluster_chol_smem(int n, int cl, int rank) {
   return (size_t)L.total() * sizeof(float);
 }
 
-// Warp 0: factor the diagonal block (rows of `blk`, stride ldb, nb valid
-// rows/columns; identity padding beyond nb) in place; its rows also go to scr.  Lane r
-// holds row r in registers; column j of the factor is published through
-// shared memory (scr row j) and read back as float4 broadcasts for the rank-1
-// update of the remaining columns.  Returns true if a pivot failed the
-// relative threshold.
-__device__ __noinline__ bool factor_diag(float* blk, int ldb, int nb, const double* diag0k,
-                                         float rel_tol, float* scr) {
-  const int lane = threadIdx.x & 31;
+// Warps 0 and 1: warp 0 factors the block (rows of blk, stride ldb, nb valid)
+// in place and writes the rows of L to scr (stride RS); warp 1 builds L^{-1}
+// into li (stride RS) one column behind, from the multipliers warp 0 hands
+// over through a two-row column buffer (col, 2 x 33 floats: 32 multipliers
+// and 1 / L[j][j]) and the 64-thread named barrier 3.
+__device__ __noinline__ bool factor_invert2(float* blk, int ldb, int nb, const double* diag0k,
+                                            float rel_tol, float* scr, float* li, float* col) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned full = 0xffffffffu;
-  float a[CB];
-#pragma unroll
-  for (int c4 = 0; c4 < CB; c4 += 4) {
-    const float4 v = lane < nb ? *reinterpret_cast<const float4*>(blk + lane * ldb + c4)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-    a[c4] = v.x;
-    a[c4 + 1] = v.y;
-    a[c4 + 2] = v.z;
-    a[c4 + 3] = v.w;
-  }
-#pragma unroll
-  for (int c = 0; c < CB; ++c)
-    if (!(lane < nb && c < nb && c <= lane)) a[c] = (c == lane) ? 1.f : 0.f;
-  const float thr = lane < nb ? (float)(rel_tol * diag0k[lane]) : 0.f;
   bool lbad = false;
-  float* ip = scr + (2 * CB - 1) * RS;  // 1 / L[j][j]
+  if (warp == 0) {
+    float a[CB];
 #pragma unroll
-  for (int j = 0; j < CB; ++j) {
-    float d = __shfl_sync(full, a[j], j);
-    const float tj = __shfl_sync(full, thr, j);
-    if (!(d > tj)) {
-      lbad |= (j < nb);
-      d = 1.f;
+    for (int c4 = 0; c4 < CB; c4 += 4) {
+      const float4 v = lane < nb ? *reinterpret_cast<const float4*>(blk + lane * ldb + c4)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+      a[c4] = v.x;
+      a[c4 + 1] = v.y;
+      a[c4 + 2] = v.z;
+      a[c4 + 3] = v.w;
     }
-    const float ipv = rsqrtf(d);
-    if (lane == 0) ip[j] = ipv;
-    const float l = (lane > j) ? a[j] * ipv : (lane == j ? d * ipv : 0.f);
-    scr[j * RS + lane] = l;  // column j of L
-    __syncwarp();
 #pragma unroll
-    for (int c4 = ((j + 1) & ~3); c4 < CB; c4 += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(scr + j * RS + c4);
-      if (c4 > j) a[c4] = fmaf(-l, v.x, a[c4]);
-      if (c4 + 1 > j) a[c4 + 1] = fmaf(-l, v.y, a[c4 + 1]);
-      if (c4 + 2 > j) a[c4 + 2] = fmaf(-l, v.z, a[c4 + 2]);
-      if (c4 + 3 > j) a[c4 + 3] = fmaf(-l, v.w, a[c4 + 3]);
+    for (int c = 0; c < CB; ++c)
+      if (!(lane < nb && c < nb && c <= lane)) a[c] = (c == lane) ? 1.f : 0.f;
+    const float thr = lane < nb ? (float)(rel_tol * diag0k[lane]) : 0.f;
+    float piv = a[0];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      float d = __shfl_sync(full, piv, j);
+      const float tj = __shfl_sync(full, thr, j);
+      if (!(d > tj)) {
+        lbad |= (j < nb);
+        d = 1.f;
+      }
+      const float rs = rsqrtf(d);
+      const float l = lane > j ? a[j] * rs : (lane == j ? d * rs : 0.f);
+      float* cj = col + (j & 1) * (CB + 4);
+      cj[lane] = l;
+      if (lane == 0) cj[CB] = rs;
+      a[j] = l;
+      if (j + 1 < CB) {
+        piv = fmaf(-l, l, a[j + 1]);
+        const float l1 = __shfl_sync(full, l, j + 1);
+        a[j + 1] = fmaf(-l, l1, a[j + 1]);
+      }
+      __syncwarp();
+      asm volatile("bar.sync 3, 64;" ::: "memory");
+#pragma unroll
+      for (int c4 = (j + 2) & ~3; c4 < CB; c4 += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(cj + c4);
+        if (c4 >= j + 2) a[c4] = fmaf(-l, v.x, a[c4]);
+        if (c4 + 1 >= j + 2) a[c4 + 1] = fmaf(-l, v.y, a[c4 + 1]);
+        if (c4 + 2 >= j + 2) a[c4 + 2] = fmaf(-l, v.z, a[c4 + 2]);
+        if (c4 + 3 >= j + 2) a[c4 + 3] = fmaf(-l, v.w, a[c4 + 3]);
+      }
     }
-    a[j] = l;
-  }
-  __syncwarp();
-  // rows of L (strict upper part zero) to scr and, for rows that exist, to blk
 #pragma unroll
-  for (int c4 = 0; c4 < CB; c4 += 4) {
-    const float4 v = make_float4(c4 <= lane ? a[c4] : 0.f, c4 + 1 <= lane ? a[c4 + 1] : 0.f,
-                                 c4 + 2 <= lane ? a[c4 + 2] : 0.f, c4 + 3 <= lane ? a[c4 + 3] : 0.f);
-    *reinterpret_cast<float4*>(scr + lane * RS + c4) = v;
-    if (lane < nb) *reinterpret_cast<float4*>(blk + lane * ldb + c4) = v;
+    for (int c4 = 0; c4 < CB; c4 += 4) {
+      const float4 v = make_float4(c4 <= lane ? a[c4] : 0.f, c4 + 1 <= lane ? a[c4 + 1] : 0.f,
+                                   c4 + 2 <= lane ? a[c4 + 2] : 0.f, c4 + 3 <= lane ? a[c4 + 3] : 0.f);
+      *reinterpret_cast<float4*>(scr + lane * RS + c4) = v;
+      if (lane < nb) *reinterpret_cast<float4*>(blk + lane * ldb + c4) = v;
+    }
+  } else {
+    // lane c: column c of L^{-1}; s[i] = sum_{q < i} L[i][q] x_q
+    float s[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) s[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      asm volatile("bar.sync 3, 64;" ::: "memory");
+      const float* cj = col + (j & 1) * (CB + 4);
+      const float rs = cj[CB];
+      const float x = ((lane == j ? 1.f : 0.f) - s[j]) * rs;
+      li[j * RS + lane] = x;
+#pragma unroll
+      for (int c4 = (j + 1) & ~3; c4 < CB; c4 += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(cj + c4);
+        if (c4 > j) s[c4] = fmaf(v.x, x, s[c4]);
+        if (c4 + 1 > j) s[c4 + 1] = fmaf(v.y, x, s[c4 + 1]);
+        if (c4 + 2 > j) s[c4 + 2] = fmaf(v.z, x, s[c4 + 2]);
+        if (c4 + 3 > j) s[c4 + 3] = fmaf(v.w, x, s[c4 + 3]);
+      }
+    }
   }
   __syncwarp();
   return __any_sync(full, lbad);
-}
-
-// Warp 0: inverse of the factored diagonal block whose rows are in scr (and
-// 1 / L[r][r] in scr row 63): lane c solves L x = e_c by forward substitution
-// (no exchange between lanes); x[r] = Linv[r][c] goes to li.
-__device__ __noinline__ void invert_diag(const float* scr, float* li) {
-  const int lane = threadIdx.x & 31;
-  const float* ip = scr + (2 * CB - 1) * RS;
-  float x[CB];
-#pragma unroll
-  for (int r = 0; r < CB; ++r) {
-    float s0 = (r == lane) ? 1.f : 0.f, s1 = 0.f;
-#pragma unroll
-    for (int q4 = 0; q4 < r; q4 += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(scr + r * RS + q4);
-      float& s = ((q4 >> 2) & 1) ? s1 : s0;
-      s = fmaf(-v.x, x[q4], s);
-      if (q4 + 1 < r) s = fmaf(-v.y, x[q4 + 1], s);
-      if (q4 + 2 < r) s = fmaf(-v.z, x[q4 + 2], s);
-      if (q4 + 3 < r) s = fmaf(-v.w, x[q4 + 3], s);
-    }
-    x[r] = (s0 + s1) * ip[r];
-  }
-#pragma unroll
-  for (int r = 0; r < CB; ++r) li[r * RS + lane] = x[r];
 }
 
 // One warp: rows [r0, r1) of a 32-row tile, out[r][c] -= sum_q P[r][q] Q[c][q]
@@ -407,9 +410,11 @@ __global__ void __launch_bounds__(CTH, 1)
     }
   }
   __syncthreads();
-  if (rank == 0 && warp == 0) {  // diagonal block 0
-    if (factor_diag(blk(0), Layout::ldb(0), nbr(0), diag0, rel_tol, scr) && tid == 0) bad = 1;
-    invert_diag(scr, lib(0));
+  if (rank == 0 && warp < 2) {  // diagonal block 0
+    if (factor_invert2(blk(0), Layout::ldb(0), nbr(0), diag0, rel_tol, scr, lib(0),
+                       scr + CB * RS) &&
+        tid == 0)
+      bad = 1;
   }
   __syncthreads();
   cluster_arrive();
@@ -473,12 +478,12 @@ __global__ void __launch_bounds__(CTH, 1)
                               warp * 8, warp * 8 + 8);
       __syncthreads();
       if (pf && tid == 0) pf[8 * k + 4] = gtime();
-      if (warp == 0) {
-        if (factor_diag(X + (k + 1) * CB, ld, nbr(k + 1), diag0 + (k + 1) * CB, rel_tol, scr) &&
+      if (warp < 2) {
+        if (factor_invert2(X + (k + 1) * CB, ld, nbr(k + 1), diag0 + (k + 1) * CB, rel_tol, scr,
+                           lib(k + 1), scr + CB * RS) &&
             tid == 0)
           bad = 1;
         if (pf && tid == 0) pf[8 * k + 7] = gtime();
-        invert_diag(scr, lib(k + 1));
       }
       __syncthreads();
       if (pf && tid == 0) pf[8 * k + 5] = gtime();
