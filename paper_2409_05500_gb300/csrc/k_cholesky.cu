@@ -40,7 +40,7 @@ namespace {
 constexpr int CB = 32;        // block column width
 constexpr int RS = CB + 4;    // shared row stride: 16-byte rows, conflict-free float4 columns
 constexpr int CL_MAX = 8;     // CTAs per cluster (portable maximum)
-constexpr int CTH = 512;      // threads per CTA
+constexpr int CTH = 384;      // threads per CTA (measured against 512 and 256)
 constexpr int CL_NMAX = 512;  // largest n handled
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -208,7 +208,7 @@ __device__ __noinline__ bool factor_invert2(float* blk, int ldb, int nb, const d
 // One warp: rows [r0, r1) of a 32-row tile, out[r][c] -= sum_q P[r][q] Q[c][q]
 // for lane c; Q rows c >= qrows count as zero.  P rows are read as float4
 // broadcasts, Q row c by lane c (stride ldq, conflict-free for ldq = 4 mod 32).
-__device__ __noinline__ void tile_rows(float* out, int ldo, const float* P, int ldp,
+__device__ __forceinline__ void tile_rows(float* out, int ldo, const float* P, int ldp,
                                           const float* Q, int ldq, int qrows, int r0, int r1) {
   const int lane = threadIdx.x & 31;
   float q[CB];
@@ -248,7 +248,7 @@ __device__ __noinline__ void tile_rows(float* out, int ldo, const float* P, int 
 
 // One warp: panel rows [r0, r1), X[r][c] = sum_{q <= c} X[r][q] Linv[c][q] in
 // place (lane c; Linv lower triangular, stride RS).
-__device__ __noinline__ void panel_tile_rows(float* X, int ldx, const float* linv, int r0,
+__device__ __forceinline__ void panel_tile_rows(float* X, int ldx, const float* linv, int r0,
                                                 int r1) {
   const int lane = threadIdx.x & 31;
   float lr[CB];
