@@ -118,6 +118,32 @@ vl_status vl_var_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, in
                      vl_precision prec, double* M, double* E);
 
 /*
+ * Lag order of the VAR by an information criterion (the paper takes p as
+ * given, Sec. 4.1; the criteria are standard VAR practice).  Every candidate
+ * p = 1..p_max is fitted as by vl_var_fit (precision prec) on the same
+ * T = n - p_max equations t = p_max..n-1, so the fits compare the same data;
+ * its ML residual covariance S(p) = E E^T / T is formed and factored in FP64,
+ * and
+ *     AIC(p) = ln det S(p) + 2 p m^2 / T
+ *     BIC(p) = ln det S(p) + ln(T) p m^2 / T
+ *     HQ(p)  = ln det S(p) + 2 ln(ln T) p m^2 / T
+ * (the m intercepts, common to every p, are left out).  The smallest value
+ * wins; ties pick the smaller p.
+ * X      : m x n, row stride ldx (device).
+ * values : output, p_max doubles (device): the criterion for p = 1..p_max.
+ * p_best : output, one int32 (device): the chosen p.
+ * Requires m >= 2, p_max >= 1 and n - p_max > m (p_max + 1), so that the
+ * largest candidate's residual covariance can be of full rank (else
+ * VL_ERR_RANK).
+ * A residual covariance that is not positive definite sets VL_ERR_RANK on
+ * the device (reported by vl_sync).  The fits' residuals and coefficients
+ * live in a buffer of the handle, allocated on the first call of a size.
+ */
+typedef enum { VL_IC_AIC = 0, VL_IC_BIC = 1, VL_IC_HQ = 2 } vl_criterion;
+vl_status vl_var_select(vl_handle h, const double* X, int64_t ldx, int m, int n, int p_max,
+                        vl_criterion crit, vl_precision prec, double* values, int32_t* p_best);
+
+/*
  * One-time pairwise precomputation (Sec. 4.2 items 1-2; Algorithm 1, the two
  * precompute calls; Eqs. 1-2 of Sec. 3).  Each row of E is standardized
  * (population variance).  For every ordered pair (i, j), i != j, the residual

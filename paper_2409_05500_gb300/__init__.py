@@ -39,7 +39,8 @@ EXPORTED = ("vl_create", "vl_destroy", "vl_set_stream", "vl_reserve", "vl_sync",
             "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_fit", "vl_var_fit",
             "vl_pairwise_measure", "vl_causal_order", "vl_causal_order_noalloc",
             "vl_causal_order_certified", "vl_causal_order_standard", "vl_fit_b",
-            "vl_fit_batched", "vl_fit_batched_async", "vl_sfu_rate")
+            "vl_fit_batched", "vl_fit_batched_async", "vl_sfu_rate", "vl_var_select")
+CRITERIA = {"aic": 0, "bic": 1, "hq": 2}
 
 
 class VLError(RuntimeError):
@@ -69,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "vl_reserve": [P, I, I, I],
         "vl_sync": [P],
         "vl_var_fit": [P, P, I64, I, I, I, I, P, P],
+        "vl_var_select": [P, P, I64, I, I, I, I, I, P, P],
         "vl_pairwise_measure": [P, P, I64, I, I, I, P, P, P],
         "vl_causal_order": [P, P, I, P, P],
         "vl_causal_order_noalloc": [P, P, I, P, P],
@@ -176,6 +178,15 @@ def vl_var_fit(h: Handle, X: torch.Tensor, p: int, prec: str, M: torch.Tensor,
     m, n = X.shape
     h.check(_lib.vl_var_fit(h.h, _ptr(X), X.stride(0), m, n, p, PRECISIONS[prec], _ptr(M),
                             _ptr(E)), "vl_var_fit")
+
+
+def vl_var_select(h: Handle, X: torch.Tensor, p_max: int, criterion: str, prec: str,
+                  values: torch.Tensor, p_best: torch.Tensor) -> None:
+    """Lag order by AIC, BIC or HQ over p = 1..p_max (see the header):
+    values (p_max FP64) and p_best (one int32) are device outputs."""
+    m, n = X.shape
+    h.check(_lib.vl_var_select(h.h, _ptr(X), X.stride(0), m, n, p_max, CRITERIA[criterion],
+                               PRECISIONS[prec], _ptr(values), _ptr(p_best)), "vl_var_select")
 
 
 def vl_pairwise_measure(h: Handle, E: torch.Tensor, prec: str, Hx: Optional[torch.Tensor],

@@ -960,6 +960,7 @@ vl_status vl_destroy(vl_handle h) {
     if (h->bstatus) cudaFree(h->bstatus);
     if (h->sbuf) cudaFree(h->sbuf);
     if (h->bbuf) cudaFree(h->bbuf);
+    if (h->selbuf) cudaFree(h->selbuf);
     if (h->blist) cudaFree(h->blist);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
@@ -1045,6 +1046,59 @@ vl_status vl_var_fit(vl_handle h, const double* X, int64_t ldx, int m, int n, in
   Exec x = handle_exec(h);
   return prec != VL_PREC_FP64 ? var_fit_impl<float>(x, X, ldx, m, n, p, M, E)
                                : var_fit_impl<double>(x, X, ldx, m, n, p, M, E);
+}
+
+vl_status vl_var_select(vl_handle h, const double* X, int64_t ldx, int m, int n, int p_max,
+                        vl_criterion crit, vl_precision prec, double* values, int32_t* p_best) {
+  if (!h) return VL_ERR_ARG;
+  if (!X || !values || !p_best)
+    return fail(h, VL_ERR_ARG, "vl_var_select: X, values and p_best must not be NULL");
+  if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
+  if (crit != VL_IC_AIC && crit != VL_IC_BIC && crit != VL_IC_HQ)
+    return fail(h, VL_ERR_ARG, "vl_var_select: unknown criterion");
+  if (m < 2 || p_max < 1 || n < 2 || m > VL_MAX_M || ldx < n)
+    return fail(h, VL_ERR_SHAPE, "vl_var_select: need m >= 2, p_max >= 1, ldx >= n");
+  const int64_t T = (int64_t)n - p_max;
+  if (T <= (int64_t)m * (p_max + 1))
+    return fail(h, VL_ERR_RANK,
+                "vl_var_select: n - p_max <= m (p_max + 1), the residual covariance of the "
+                "largest VAR cannot be of full rank");
+  DeviceGuard g(h->device);
+  Exec x = handle_exec(h);
+  // the candidates' coefficients and residuals (reused from p to p)
+  const size_t mb = (size_t)p_max * m * m, eb = (size_t)m * T;
+  vl_status s = grow(h, &h->selbuf, &h->selbuf_cap, sizeof(double) * (mb + eb) + 512, x.s);
+  if (s != VL_OK) return s;
+  double* Mb = static_cast<double*>(h->selbuf);
+  double* Eb = Mb + mb;
+  const double lt = std::log((double)T);
+  const double pen = crit == VL_IC_AIC ? 2.0 : (crit == VL_IC_BIC ? lt : 2.0 * std::log(lt));
+  const int nblk = (m + CHOL_NB - 1) / CHOL_NB;
+  const size_t part_cap = std::max((size_t)16 * m * m, gemm_part_need(m, m, (int)T));
+  for (int p = 1; p <= p_max; ++p) {
+    // candidate p on the columns p_max - p .. n-1: residuals for t = p_max .. n-1
+    const double* Xp = X + (p_max - p);
+    const int np = (int)T + p;
+    s = prec != VL_PREC_FP64 ? var_fit_impl<float>(x, Xp, ldx, m, np, p, Mb, Eb)
+                             : var_fit_impl<double>(x, Xp, ldx, m, np, p, Mb, Eb);
+    if (s != VL_OK) return s;
+    // S = E E^T / T and its Cholesky factor, in FP64; ln det S from the diagonal
+    double *S, *dinv, *diag0, *part;
+    s = with_workspace(x, [&](Arena& a) {
+      S = a.take<double>((size_t)m * m);
+      dinv = a.take<double>((size_t)nblk * CHOL_NB * CHOL_NB);
+      diag0 = a.take<double>(m);
+      part = a.take<double>(part_cap);
+    });
+    if (s != VL_OK) return s;
+    Ctx cx = make_ctx(x, part, part_cap);
+    View<double> Ev{Eb, T, 1};
+    launch_gemm<double, double>(cx, m, m, (int)T, 1.0 / (double)T, Ev, Ev, 0.0, S, m, false);
+    chol_blocked<double>(cx, S, m, m, dinv, diag0);
+    launch_logdet_value(S, m, m, pen * p * (double)m * m / (double)T, values + (p - 1), x.st, x.s);
+  }
+  launch_argmin_p(values, p_max, p_best, x.s);
+  return check_launch(h, "vl_var_select");
 }
 
 vl_status vl_pairwise_measure(vl_handle h, const double* E, int64_t lde, int m, int n_eff,

@@ -344,4 +344,46 @@ template void launch_transpose_std<float>(const double*, int64_t, int, int, cons
 template void launch_transpose_std<double>(const double*, int64_t, int, int, const double*,
                                            const double*, double*, int, int, cudaStream_t);
 
+namespace {
+
+// One CTA: 2 sum ln L[i][i] in FP64 (a fixed-order block reduction).
+__global__ void logdet_value_kernel(const double* __restrict__ L, int64_t ldl, int m,
+                                    double penalty, double* __restrict__ value, int* st) {
+  __shared__ double red[32];
+  double s = 0.0;
+  bool bad = false;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double d = L[(int64_t)i * ldl + i];
+    bad |= !(d > 0.0);
+    s += d > 0.0 ? log(d) : 0.0;
+  }
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) set_status(st, VL_ERR_RANK);
+    return;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *value = 2.0 * s + penalty;
+}
+
+__global__ void argmin_p_kernel(const double* __restrict__ values, int p_max,
+                                int32_t* __restrict__ p_best) {
+  int best = 0;
+  for (int i = 1; i < p_max; ++i)
+    if (values[i] < values[best]) best = i;
+  *p_best = best + 1;
+}
+
+}  // namespace
+
+void launch_logdet_value(const double* L, int64_t ldl, int m, double penalty, double* value,
+                         int* st, cudaStream_t s) {
+  note_launch();
+  logdet_value_kernel<<<1, kStatThreads, 0, s>>>(L, ldl, m, penalty, value, st);
+}
+
+void launch_argmin_p(const double* values, int p_max, int32_t* p_best, cudaStream_t s) {
+  note_launch();
+  argmin_p_kernel<<<1, 1, 0, s>>>(values, p_max, p_best);
+}
+
 }  // namespace vl

@@ -86,6 +86,8 @@ struct vl_handle_s {
   // and the autotuner's cache (batch signature -> samples per split)
   void* bbuf = nullptr;
   size_t bbuf_cap = 0;
+  void* selbuf = nullptr;  // lag selection: coefficients and residuals of the fits
+  size_t selbuf_cap = 0;
   void* blist = nullptr;
   size_t blist_cap = 0;
   unsigned long long blist_sig = 0;
@@ -140,6 +142,13 @@ void launch_var_cst(const T* beta, int m, int p, const double* wbar, double* cst
 // CTAs per output tile (refine_splits(m, p, num_sms) of them); part holds
 // that many m p x m blocks of float2 partial sums.
 constexpr int REFINE_MAX_SPLITS = 8;
+// Lag selection: values[0] = 2 sum_i ln L[i][i] + penalty for the Cholesky
+// factor L (lower part of L, row stride ldl) of the residual covariance; a
+// non-positive diagonal sets VL_ERR_RANK.  Then p_best = 1 + argmin of the
+// p_max values (ties: smaller p).
+void launch_logdet_value(const double* L, int64_t ldl, int m, double penalty, double* value,
+                         int* st, cudaStream_t s);
+void launch_argmin_p(const double* values, int p_max, int32_t* p_best, cudaStream_t s);
 int refine_splits(int m, int p, int num_sms);
 void launch_refine_residual(const float* nhi, const float* nlo, int m, int p, const float* beta0,
                             float* r, float2* part, int num_sms, cudaStream_t s);

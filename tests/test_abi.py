@@ -79,6 +79,8 @@ def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
         "vl_sync": ([P], [None]),
         "vl_profile_events": ([P, P, P], [None, None, None]),
         "vl_var_fit": ([P, P, I64, I, I, I, I, P, P], [None, None, 100, 10, 100, 1, 1, None, None]),
+        "vl_var_select": ([P, P, I64, I, I, I, I, I, P, P],
+                          [None, None, 100, 10, 100, 2, 1, 1, None, None]),
         "vl_pairwise_measure": ([P, P, I64, I, I, I, P, P, P],
                                 [None, None, 100, 10, 100, 1, None, None, None]),
         "vl_causal_order": ([P, P, I, P, P], [None, None, 10, None, None]),
