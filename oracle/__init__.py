@@ -26,6 +26,9 @@ Contents (all in :mod:`oracle.fp64`):
 * ``b0_ols`` / ``b0_ldl`` two independent routes to B0 from a causal order.
 * ``btau``               B_tau = (I - B0) M_tau.
 * ``varlingam``          the whole pipeline, heuristic or standard.
+* ``bootstrap``          the pipeline on moving-block resamples of the series
+                         (a reading: the paper specifies no resampling), with
+                         the counter-based generator ``splitmix64_draw``.
 
 :mod:`oracle.parallel` runs the same functions with the rows of E_r on a
 process pool, only to time the oracle on all host cores (its results are the
@@ -45,6 +48,8 @@ from .fp64 import (  # noqa: F401
     H_GAUSS,
     b0_ldl,
     b0_ols,
+    bootstrap,
+    bootstrap_indices,
     btau,
     entropy,
     logcosh,
@@ -57,6 +62,8 @@ from .fp64 import (  # noqa: F401
     residual,
     score,
     scores_over,
+    splitmix64,
+    splitmix64_draw,
     standardize,
     var_ols,
     var_select,

@@ -424,3 +424,75 @@ def varlingam(X: np.ndarray, p: int, method: str = "heuristic") -> Dict[str, obj
     out["B0"] = B0
     out["Btau"] = btau(B0, M)
     return out
+
+
+# ------------------------------------------------------------ bootstrap
+# Bootstrap resampling of the batched path (the paper does not specify one;
+# the reading is the moving-block bootstrap of Kuensch, Ann. Statist. 1989,
+# the usual resampling for a dependent series).  Its random block starts are
+# drawn from a counter-based generator written here from its published
+# definition, the SplitMix64 output function (Steele, Lea and Flood, OOPSLA
+# 2014), so that any draw can be produced independently of the others.
+MASK64 = (1 << 64) - 1
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64(state: int) -> int:
+    """The SplitMix64 output for a state already advanced by the gamma:
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9; z = (z ^ (z >> 27)) *
+    0x94D049BB133111EB; z ^ (z >> 31), all modulo 2^64."""
+    z = state & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def splitmix64_draw(seed: int, counter: int) -> int:
+    """Output number `counter` (1, 2, ...) of SplitMix64 seeded with `seed`:
+    the state after `counter` steps is seed + counter * gamma."""
+    return splitmix64((seed + counter * SPLITMIX_GAMMA) & MASK64)
+
+
+def bootstrap_indices(n: int, block_len: int, seed: int, b: int) -> np.ndarray:
+    """Time indices of moving-block resample b of a series of length n: blocks
+    k = 0, 1, .. of block_len consecutive indices starting at
+    s_k = floor(u_k (n - block_len + 1) / 2^64), u_k = draw b 2^32 + k + 1 of
+    the generator, concatenated and cut to n."""
+    if not 1 <= block_len <= n:
+        raise ValueError("need 1 <= block_len <= n")
+    span = n - block_len + 1
+    idx = np.empty(n, dtype=np.int64)
+    for t in range(n):
+        k, off = divmod(t, block_len)
+        u = splitmix64_draw(seed, (b << 32) + k + 1)
+        idx[t] = ((u * span) >> 64) + off
+    return idx
+
+
+def bootstrap(X: np.ndarray, p: int, n_resamples: int, block_len: int, seed: int,
+              threshold: float, method: str = "heuristic") -> Dict[str, object]:
+    """The whole method on every resample b = 0..n_resamples-1 (resample b is
+    X[:, bootstrap_indices(n, block_len, seed, b)]), then
+        edge_prob[i, j]  = fraction of resamples with |B0[i, j]| > threshold,
+        order_prob[i, j] = fraction of resamples in which i precedes j in the
+                           causal order (0 on the diagonal);
+    also the per-resample orders, B0 and smallest relative score gap of the
+    search (for comparisons that must allow near ties)."""
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    edge = np.zeros((m, m))
+    before = np.zeros((m, m))
+    orders, B0s, gaps = [], [], []
+    for b in range(n_resamples):
+        r = varlingam(X[:, bootstrap_indices(n, block_len, seed, b)], p, method)
+        order = [int(c) for c in r["order"]]
+        pos = np.empty(m, dtype=np.int64)
+        pos[order] = np.arange(m)
+        edge += np.abs(r["B0"]) > threshold
+        before += pos[:, None] < pos[None, :]
+        orders.append(order)
+        B0s.append(r["B0"])
+        gaps.append(min([relative_gap(st["scores"]) for st in r["steps"][:-1]] or [math.inf]))
+    return {"edge_prob": edge / n_resamples, "order_prob": before / n_resamples,
+            "orders": orders, "B0s": B0s, "min_gaps": gaps}
+
