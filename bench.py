@@ -52,6 +52,52 @@ PAIRWISE_TRAFFIC = {"sha1": "4487adf570f6a73e667881749b8d39d88d1a9251",
                     "bytes": 4917760 + 9472, "m": 400, "n": 2500}
 
 
+def run_bootstrap(vl, h, torch, dev, inst, Xd):
+    """The moving-block bootstrap of the bench workload: 64 resamples in
+    blocks of 100 time points, each fitted by the certified mixed batch, and
+    the edge (|B0| > 0.05) and order probabilities over them: one vl_bootstrap
+    call after an untimed one (which sizes the buffers and tunes the batch).
+    Also the resampling gather alone (vl_bootstrap_resample of the 64
+    resamples: 8 m n bytes written per resample, the series itself read once
+    from HBM and then from L2), the median of 5.  CUDA events on the
+    handle's stream."""
+    m, n = inst.X.shape
+    B, L = 64, 100
+    f64 = dict(dtype=torch.float64, device=f"cuda:{dev}")
+    ep, op = torch.empty((m, m), **f64), torch.empty((m, m), **f64)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    vl.vl_bootstrap(h, Xd, inst.p, B, L, 1, 0.05, "mixed_certified", ep, op)
+    h.sync()
+    a, b = ev(), ev()
+    a.record(h.stream)
+    vl.vl_bootstrap(h, Xd, inst.p, B, L, 1, 0.05, "mixed_certified", ep, op)
+    b.record(h.stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b)
+    Xb = torch.empty((B, m, n), **f64)
+    ms = []
+    for _ in range(6):
+        a, b = ev(), ev()
+        a.record(h.stream)
+        vl.vl_bootstrap_resample(h, Xd, L, 1, 0, Xb)
+        b.record(h.stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    tr = statistics.median(ms[1:])
+    gb = 8 * (B + 1) * m * n / 1e9
+    del Xb
+    return {"resamples": B, "block_len": L, "prec": "mixed_certified", "ms": round(t, 3),
+            "resamples_per_s": round(B / (t * 1e-3), 1),
+            "value": B * pair_samples(m, n, inst.p) / (t * 1e-3), "unit": UNIT,
+            "resample_kernel": {"ms": round(tr, 4), "GB": round(gb, 3),
+                                "GB_per_s": round(gb / (tr * 1e-3), 1)},
+            "timing": "one vl_bootstrap call after an untimed one; the gather alone, "
+                      "median of 5 after one"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -70,6 +116,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip timing the 256-series mixed-size batch")
+    ap.add_argument("--no-bootstrap", action="store_true",
+                    help="skip timing the moving-block bootstrap of the workload")
     return ap.parse_args()
 
 
@@ -485,6 +533,8 @@ def run_ours(args, rank, world):
     }
     if not args.no_batched:
         res["batched"] = run_batched(vl, h, torch, dev, args, stream)
+    if not args.no_bootstrap:
+        res["bootstrap"] = run_bootstrap(vl, h, torch, dev, inst, X)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
         try:

@@ -337,6 +337,42 @@ vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_pre
 vl_status vl_fit_batched_async(vl_handle h, const vl_instance* inst, int count,
                                vl_precision prec, int32_t* dev_status);
 
+/*
+ * Bootstrap (no counterpart in the paper, which reports single fits): the
+ * moving-block bootstrap of Kuensch (1989), which keeps the serial
+ * dependence a VAR model relies on within blocks of block_len consecutive
+ * time points.  Resample b (0 <= b < 2^32) of the m x n series is the
+ * concatenation of blocks k = 0, 1, ... starting at time
+ *   s_k = floor(u_k (n - block_len + 1) / 2^64),
+ * cut to n points, where u_k is output number b 2^32 + k + 1 of SplitMix64
+ * (Steele, Lea and Flood 2014) seeded with `seed`:
+ *   u = mix(seed + c * 0x9E3779B97F4A7C15) mod 2^64 for output number c.
+ * The generator is counter based, so resample b is the same however many
+ * resamples a call asks for.
+ *
+ * vl_bootstrap_resample: resamples b0 .. b0 + nb - 1 of X (device, m x n,
+ * row stride ldx) into Xb (device, nb blocks of m x n, row stride n, block z
+ * = resample b0 + z).  Needs 1 <= block_len <= n and b0 + nb <= 2^32 (else
+ * VL_ERR_SHAPE).  Asynchronous on the handle's stream; allocates nothing.
+ *
+ * vl_bootstrap: the whole method (vl_fit, steps 1-4) on resamples
+ * 0 .. n_resamples - 1 and, over them (device outputs, m x m row-major),
+ *   edge_prob[i][j]  = fraction of resamples with |B0[i][j]| > threshold,
+ *   order_prob[i][j] = fraction of resamples whose causal order puts i
+ *                      before j (0 on the diagonal).
+ * The resamples are fitted in chunks through the batched path
+ * (vl_fit_batched) in the given precision, in a handle-owned buffer of at
+ * most about 2 GiB; the call synchronises the stream after every chunk.
+ * The first failed fit of a resample fails the call with its status.
+ * Needs m >= 2, p >= 1, n - p > m p + 1 (else VL_ERR_RANK), threshold >= 0
+ * (else VL_ERR_ARG).
+ */
+vl_status vl_bootstrap_resample(vl_handle h, const double* X, int64_t ldx, int m, int n,
+                                int block_len, uint64_t seed, int64_t b0, int nb, double* Xb);
+vl_status vl_bootstrap(vl_handle h, const double* X, int64_t ldx, int m, int n, int p,
+                       int n_resamples, int block_len, uint64_t seed, double threshold,
+                       vl_precision prec, double* edge_prob, double* order_prob);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,8 @@ EXPORTED = ("vl_create", "vl_destroy", "vl_set_stream", "vl_reserve", "vl_sync",
             "vl_last_error", "vl_profile_events", "vl_kernel_launches", "vl_fit", "vl_var_fit",
             "vl_pairwise_measure", "vl_causal_order", "vl_causal_order_noalloc",
             "vl_causal_order_certified", "vl_causal_order_standard", "vl_fit_b",
-            "vl_fit_batched", "vl_fit_batched_async", "vl_sfu_rate", "vl_var_select")
+            "vl_fit_batched", "vl_fit_batched_async", "vl_sfu_rate", "vl_var_select",
+            "vl_bootstrap_resample", "vl_bootstrap")
 CRITERIA = {"aic": 0, "bic": 1, "hq": 2}
 
 
@@ -71,6 +72,8 @@ def _load() -> ctypes.CDLL:
         "vl_sync": [P],
         "vl_var_fit": [P, P, I64, I, I, I, I, P, P],
         "vl_var_select": [P, P, I64, I, I, I, I, I, P, P],
+        "vl_bootstrap_resample": [P, P, I64, I, I, I, ctypes.c_uint64, I64, I, P],
+        "vl_bootstrap": [P, P, I64, I, I, I, I, I, ctypes.c_uint64, ctypes.c_double, I, P, P],
         "vl_pairwise_measure": [P, P, I64, I, I, I, P, P, P],
         "vl_causal_order": [P, P, I, P, P],
         "vl_causal_order_noalloc": [P, P, I, P, P],
@@ -123,6 +126,16 @@ def _ptr(t: Optional[torch.Tensor]):
         raise ValueError("library arguments must be CUDA tensors")
     if not t.is_contiguous():
         raise ValueError("library arguments must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _rows_ptr(t: torch.Tensor):
+    """A matrix whose rows may be strided (a column slice of a wider one):
+    unit stride within a row, the row stride passed beside the pointer."""
+    if not t.is_cuda:
+        raise ValueError("library arguments must be CUDA tensors")
+    if t.dim() != 2 or t.stride(1) != 1 or t.stride(0) < t.shape[1]:
+        raise ValueError("matrix arguments need unit stride within a row")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -187,6 +200,28 @@ def vl_var_select(h: Handle, X: torch.Tensor, p_max: int, criterion: str, prec: 
     m, n = X.shape
     h.check(_lib.vl_var_select(h.h, _ptr(X), X.stride(0), m, n, p_max, CRITERIA[criterion],
                                PRECISIONS[prec], _ptr(values), _ptr(p_best)), "vl_var_select")
+
+
+def vl_bootstrap_resample(h: Handle, X: torch.Tensor, block_len: int, seed: int, b0: int,
+                          Xb: torch.Tensor) -> None:
+    """Moving-block resamples b0 .. b0 + nb - 1 of X into Xb (nb x m x n,
+    contiguous; see the header for the block starts)."""
+    m, n = X.shape
+    nb = Xb.shape[0]
+    h.check(_lib.vl_bootstrap_resample(h.h, _rows_ptr(X), X.stride(0), m, n, block_len, seed, b0, nb,
+                                       _ptr(Xb)), "vl_bootstrap_resample")
+
+
+def vl_bootstrap(h: Handle, X: torch.Tensor, p: int, n_resamples: int, block_len: int,
+                 seed: int, threshold: float, prec: str, edge_prob: torch.Tensor,
+                 order_prob: torch.Tensor) -> None:
+    """The whole method on n_resamples moving-block resamples: edge_prob and
+    order_prob (m x m FP64, device) receive the fraction of resamples with
+    |B0[i, j]| > threshold and with i before j in the causal order."""
+    m, n = X.shape
+    h.check(_lib.vl_bootstrap(h.h, _rows_ptr(X), X.stride(0), m, n, p, n_resamples, block_len, seed,
+                              threshold, PRECISIONS[prec], _ptr(edge_prob), _ptr(order_prob)),
+            "vl_bootstrap")
 
 
 def vl_pairwise_measure(h: Handle, E: torch.Tensor, prec: str, Hx: Optional[torch.Tensor],

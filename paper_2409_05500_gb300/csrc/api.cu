@@ -961,6 +961,7 @@ vl_status vl_destroy(vl_handle h) {
     if (h->sbuf) cudaFree(h->sbuf);
     if (h->bbuf) cudaFree(h->bbuf);
     if (h->selbuf) cudaFree(h->selbuf);
+    if (h->bootbuf) cudaFree(h->bootbuf);
     if (h->blist) cudaFree(h->blist);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
@@ -1221,6 +1222,72 @@ vl_status vl_fit_batched(vl_handle h, const vl_instance* inst, int count, vl_pre
   if (count == 0) return VL_OK;
   DeviceGuard g(h->device);
   return batched_impl(h, inst, count, prec, inst_status);
+}
+
+vl_status vl_bootstrap_resample(vl_handle h, const double* X, int64_t ldx, int m, int n,
+                                int block_len, uint64_t seed, int64_t b0, int nb, double* Xb) {
+  if (!h) return VL_ERR_ARG;
+  if (!X || !Xb) return fail(h, VL_ERR_ARG, "vl_bootstrap_resample: X and Xb must not be NULL");
+  if (m < 1 || n < 1 || nb < 0 || ldx < n || block_len < 1 || block_len > n)
+    return fail(h, VL_ERR_SHAPE, "vl_bootstrap_resample: need m, n >= 1, 1 <= block_len <= n");
+  if (b0 < 0 || b0 + nb > ((int64_t)1 << 32))
+    return fail(h, VL_ERR_SHAPE, "vl_bootstrap_resample: need 0 <= b0, b0 + nb <= 2^32");
+  if (nb == 0) return VL_OK;
+  DeviceGuard g(h->device);
+  launch_boot_resample(X, ldx, m, n, block_len, seed, b0, nb, Xb, h->stream);
+  return check_launch(h, "vl_bootstrap_resample");
+}
+
+vl_status vl_bootstrap(vl_handle h, const double* X, int64_t ldx, int m, int n, int p,
+                       int n_resamples, int block_len, uint64_t seed, double threshold,
+                       vl_precision prec, double* edge_prob, double* order_prob) {
+  if (!h) return VL_ERR_ARG;
+  if (!X || !edge_prob || !order_prob)
+    return fail(h, VL_ERR_ARG, "vl_bootstrap: X, edge_prob and order_prob must not be NULL");
+  if (validate_prec(h, prec) != VL_OK) return VL_ERR_ARG;
+  if (!(threshold >= 0.0)) return fail(h, VL_ERR_ARG, "vl_bootstrap: threshold must be >= 0");
+  if (m < 2 || p < 1 || n < 2 || m > VL_MAX_M || ldx < n || block_len < 1 || block_len > n ||
+      n_resamples < 1)
+    return fail(h, VL_ERR_SHAPE,
+                "vl_bootstrap: need m >= 2, p >= 1, 1 <= block_len <= n, n_resamples >= 1");
+  if ((int64_t)n - p <= (int64_t)m * p + 1)
+    return fail(h, VL_ERR_RANK, "vl_bootstrap: n - p <= m p + 1, the VAR has no unique fit");
+  DeviceGuard g(h->device);
+  // a chunk of resamples with their fits: X_b, B0, B_tau, M, order, pos
+  const size_t mm = (size_t)m * m;
+  const size_t per = sizeof(double) * ((size_t)m * n + mm * (1 + 2 * (size_t)p)) +
+                     2 * sizeof(int32_t) * m + 4 * 256;
+  const size_t budget = (size_t)2 << 30;
+  const int chunk = (int)std::min<size_t>({(size_t)n_resamples, (size_t)256,
+                                           std::max<size_t>(1, budget / per)});
+  vl_status s = grow(h, &h->bootbuf, &h->bootbuf_cap, per * chunk + 1024, h->stream);
+  if (s != VL_OK) return s;
+  Arena a;
+  a.base = static_cast<char*>(h->bootbuf);
+  a.cap = h->bootbuf_cap;
+  double* Xb = a.take<double>((size_t)chunk * m * n);
+  double* B0 = a.take<double>((size_t)chunk * mm);
+  double* Bt = a.take<double>((size_t)chunk * p * mm);
+  double* M = a.take<double>((size_t)chunk * p * mm);
+  int32_t* order = a.take<int32_t>((size_t)chunk * m);
+  int32_t* pos = a.take<int32_t>((size_t)chunk * m);
+  cudaMemsetAsync(edge_prob, 0, sizeof(double) * mm, h->stream);
+  cudaMemsetAsync(order_prob, 0, sizeof(double) * mm, h->stream);
+  std::vector<vl_instance> inst(chunk);
+  std::vector<vl_status> ist(chunk);
+  for (int b0 = 0; b0 < n_resamples; b0 += chunk) {
+    const int nb = std::min(chunk, n_resamples - b0);
+    launch_boot_resample(X, ldx, m, n, block_len, seed, b0, nb, Xb, h->stream);
+    for (int z = 0; z < nb; ++z)
+      inst[z] = vl_instance{Xb + (size_t)z * m * n, n, m, n, p, order + (size_t)z * m,
+                            B0 + z * mm, Bt + z * p * mm, M + z * p * mm, nullptr};
+    s = batched_impl(h, inst.data(), nb, prec, ist.data());
+    if (s != VL_OK) return s;
+    launch_boot_count(order, B0, m, nb, threshold, pos, edge_prob, order_prob, h->status,
+                      h->stream);
+  }
+  launch_boot_normalize(edge_prob, order_prob, m, n_resamples, h->stream);
+  return check_launch(h, "vl_bootstrap");
 }
 
 }  // extern "C"

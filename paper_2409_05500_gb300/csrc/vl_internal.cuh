@@ -88,6 +88,8 @@ struct vl_handle_s {
   size_t bbuf_cap = 0;
   void* selbuf = nullptr;  // lag selection: coefficients and residuals of the fits
   size_t selbuf_cap = 0;
+  void* bootbuf = nullptr;  // bootstrap: a chunk of resamples and their fits
+  size_t bootbuf_cap = 0;
   void* blist = nullptr;
   size_t blist_cap = 0;
   unsigned long long blist_sig = 0;
@@ -306,6 +308,18 @@ void launch_std_score_pick(const double* D, int u, double* S, unsigned* counter,
 void launch_std_refine(const double* W, int64_t ldw, int u, int n, const double* C,
                        const int* pick, const int32_t* idx, double* Wn, int64_t ldn,
                        int32_t* idx_next, int32_t* order, double* gap, int k, cudaStream_t s);
+
+// Bootstrap (k_boot.cu).  resample: out[z] (m x n, row stride n) = moving-
+// block resample b0 + z of X for z < nb.  count: with pos (nb x m scratch),
+// edge[i][j] += #{z : |B0_z[i][j]| > threshold}, before[i][j] += #{z : i
+// precedes j in order_z} over the nb fits (order nb x m, B0 nb x m x m).
+// normalize: both tables divided by count.
+void launch_boot_resample(const double* X, int64_t ldx, int m, int n, int block_len,
+                          unsigned long long seed, long long b0, int nb, double* out,
+                          cudaStream_t s);
+void launch_boot_count(const int32_t* order, const double* B0, int m, int nb, double threshold,
+                       int32_t* pos, double* edge, double* before, int* st, cudaStream_t s);
+void launch_boot_normalize(double* edge, double* before, int m, int count, cudaStream_t s);
 
 // B0 / B_tau helpers (k_fitb.cu)
 template <class T>

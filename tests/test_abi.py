@@ -94,6 +94,10 @@ def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
                    [None, None, 100, 10, 100, 1, 1, None, None, None, None, None]),
         "vl_fit_batched": ([P, P, I, I, P], [None, None, 1, 1, None]),
         "vl_fit_batched_async": ([P, P, I, I, P], [None, None, 1, 1, None]),
+        "vl_bootstrap_resample": ([P, P, I64, I, I, I, ctypes.c_uint64, I64, I, P],
+                                  [None, None, 100, 10, 100, 10, 1, 0, 1, None]),
+        "vl_bootstrap": ([P, P, I64, I, I, I, I, I, ctypes.c_uint64, ctypes.c_double, I, P, P],
+                         [None, None, 100, 10, 100, 1, 4, 10, 1, 0.1, 1, None, None]),
     }
     handle_calls = [n for n in declared_functions()
                     if n not in ("vl_create", "vl_kernel_launches", "vl_last_error",
