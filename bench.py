@@ -438,7 +438,7 @@ def run_ours(args, rank, world):
             mc = timed_graph("mixed_certified", max(3, min(20, args.steps)), 2)
         st = vl.fit(h, X, p, prec="mixed_certified", steps=True)["cert_stats"].cpu().tolist()
         certified = {"ms_per_step": round(statistics.median(mc), 4),
-                     "steps_redecided": st[0], "pairs_fp64": st[1], "picks_changed": st[2],
+                     "steps_redecided": st[0], "pairs_reevaluated": st[1], "picks_changed": st[2],
                      "steps_unverified": st[3]}
 
     # end to end through the C ABI with host buffers: pinned X in, order,

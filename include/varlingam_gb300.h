@@ -61,7 +61,7 @@ typedef enum {
 
 /* VL_PREC_MIXED_CERTIFIED computes like VL_PREC_MIXED and, in the calls that
  * order (vl_fit, vl_fit_batched), decides every near tie of Eq. 3 on entries
- * of D re-evaluated in FP64 (see vl_causal_order_certified). */
+ * of D re-evaluated to FP64 accuracy (see vl_causal_order_certified). */
 typedef enum { VL_PREC_FP64 = 0, VL_PREC_MIXED = 1, VL_PREC_MIXED_CERTIFIED = 2 } vl_precision;
 
 /* Largest m any call accepts (the ordering kernel keeps m scores per CTA). */
@@ -173,16 +173,20 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
 
 /*
  * Algorithm 1 over a D measured in VL_PREC_MIXED, with its near ties decided
- * in FP64 (Algorithm 1 and Eq. 3; Eqs. 1-2 for the re-evaluated entries).
+ * to FP64 accuracy (Algorithm 1 and Eq. 3; Eqs. 1-2 for the re-evaluated
+ * entries).
  * The FP32 measure carries errors of about 1e-6 of max|D|, which move the
  * scores of Eq. 3 by about 5e-5 relative; two candidates closer than that may
  * swap.  After the search on D, every step whose picked score and some other
  * candidate's score overlap within their error bands
  *     band(S) = 1e-3 S + 1e-5 max|D| sqrt(S) + u (1e-5 max|D|)^2
  * (u = variables remaining) is re-decided on exact scores: the entries D_ij
- * of its candidates against the remaining variables are recomputed in FP64
- * from E (standardization, rho, both standardized residuals, their entropies),
- * the scores summed in FP64, and the argmin taken (ties: lowest index).  If a
+ * of its candidates against the remaining variables are recomputed from E:
+ * the standardization in FP64, rho, both standardized residuals and the
+ * per-sample functions of their entropies in double-float arithmetic (pairs
+ * of FP32 numbers, about 48 bits; the per-sample values within 3e-14 of
+ * FP64), the sums, entropies and scores in FP64, and the argmin taken (ties:
+ * lowest index).  If a
  * pick changes, the search resumes from that step with the corrected pick and
  * the steps after it are checked again (up to three rounds).  The result is
  * then the order Algorithm 1 gives on the FP64 measure wherever the FP64
@@ -191,11 +195,11 @@ vl_status vl_causal_order(vl_handle h, const double* D, int m, int32_t* order, d
  * E     : the m x n_eff data D was measured from, row stride lde >= n_eff.
  * order : output m int32.   gap : output m doubles or NULL (as vl_causal_order,
  *         from the FP32 scores of the final order).
- * stats : output 4 int32 (device) or NULL: steps re-decided, pairs re-evaluated
- *         in FP64, picks changed, steps left as the FP32 search took them
+ * stats : output 4 int32 (device) or NULL: steps re-decided, pairs re-evaluated,
+ *         picks changed, steps left as the FP32 search took them
  *         (more than 16 candidates, or after a change in the last round).
- * Asynchronous, no host synchronisation; workspace about 12 m^2 bytes plus
- * the ordering's.  Requires 2 <= m <= VL_MAX_M, n_eff >= 2.
+ * Asynchronous, no host synchronisation; workspace about 12 m^2 + 8 m n_eff
+ * bytes plus the ordering's.  Requires 2 <= m <= VL_MAX_M, n_eff >= 2.
  */
 vl_status vl_causal_order_certified(vl_handle h, const double* D, const double* E, int64_t lde,
                                     int m, int n_eff, int32_t* order, double* gap,

