@@ -307,7 +307,7 @@ typedef struct {
  * The whole method (steps 1-4 above) for `count` independent series of
  * possibly different (m, n, p).  Mixed precisions run the phase-major batch
  * of vl_fit_batched_async; VL_PREC_FP64 deals the series, largest first, to a
- * pool of up to 8 streams forked from the handle's stream and joined back
+ * pool of up to 32 streams forked from the handle's stream and joined back
  * into it; each stream has its own workspace.  inst and inst_status are HOST
  * arrays of length count; inst_status[k] receives the instance's own status
  * after the call has completed (the call synchronises the stream).  An

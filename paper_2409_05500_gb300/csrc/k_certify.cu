@@ -141,9 +141,10 @@ __global__ void cert_round_kernel(const int32_t* __restrict__ order, int m, int 
 // the band widened by 1e-3 of itself (at least 1e-6 of the score, several
 // times FP32's rounding error), so the test flags every step the exact
 // comparison would.  One warp per block, so the m independent replays spread
-// over ceil(m / 32) SMs; the order is staged in shared memory and the P
-// entries of the next eight steps are loaded while the current eight are
-// replayed.
+// over ceil(m / 32) SMs; the order and the thresholds are staged in shared
+// memory (a threshold load from L2 on every step put ~400 clocks of latency
+// on each step's branch) and the P entries of the next eight steps are
+// loaded while the current eight are replayed.
 constexpr int FLAG_GROUP = 8;
 
 __device__ __forceinline__ void flag_load(const float* __restrict__ pth,
@@ -164,9 +165,13 @@ __global__ void __launch_bounds__(32)
                      const float* __restrict__ thr, int m, int* ctrl,
                      const unsigned long long* __restrict__ dmax_bits, int* __restrict__ flag,
                      int* __restrict__ ccount, int* __restrict__ cand) {
-  extern __shared__ int ord_s[];  // m entries
+  extern __shared__ int ord_s[];  // m order entries, then m thresholds
+  float* thr_s = reinterpret_cast<float*>(ord_s + m);
   if (!ctrl[C_ACTIVE]) return;
-  for (int t = threadIdx.x; t < m; t += blockDim.x) ord_s[t] = order[t];
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    ord_s[t] = order[t];
+    thr_s[t] = thr[t];
+  }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
@@ -178,22 +183,27 @@ __global__ void __launch_bounds__(32)
   if (pi > 0) flag_load(pth, ptl, ord_s, m, i, pi, 0, ph, pl);
   for (int t0 = 0; t0 < pi; t0 += FLAG_GROUP) {
     if (t0 + FLAG_GROUP < pi) flag_load(pth, ptl, ord_s, m, i, pi, t0 + FLAG_GROUP, nh, nl);
+    // the group's scores first (the only dependent chain), then its tests
+    float sf[FLAG_GROUP];
+#pragma unroll
+    for (int u = 0; u < FLAG_GROUP; ++u) {
+      sf[u] = s.hi + s.lo;
+      s = df::add(s, df::F2{-ph[u], -pl[u]});
+    }
 #pragma unroll
     for (int u = 0; u < FLAG_GROUP; ++u) {
       const int k = t0 + u;
       if (k >= pi) break;
       if (k >= k0) {
-        const float sf = s.hi + s.lo;
-        const float band = ((float)CERT_TAU * fabsf(sf) + bc * sqrtf(fmaxf(sf, 0.0f)) +
+        const float band = ((float)CERT_TAU * fabsf(sf[u]) + bc * sqrtf(fmaxf(sf[u], 0.0f)) +
                             (float)(m - k) * be * be) * 1.001f;
-        if (sf - band <= thr[k]) {
+        if (sf[u] - band <= thr_s[k]) {
           flag[k] = 1;
           ctrl[C_ANY] = 1;
           const int slot = atomicAdd(&ccount[k], 1);
           if (slot < CMAX) cand[(int64_t)k * CMAX + slot] = i;
         }
       }
-      s = df::add(s, df::F2{-ph[u], -pl[u]});
     }
 #pragma unroll
     for (int u = 0; u < FLAG_GROUP; ++u) {
@@ -509,7 +519,7 @@ void launch_certify(const double* D, const double* E, int64_t lde, int m, int n,
     cert_round_kernel<<<gb, 256, 0, s>>>(order, m, r, w.ctrl, w.pos, w.flag, w.ccount, w.spick,
                                          w.dmax, w.thr);
     note_launch();
-    cert_flag_kernel<<<(m + 31) / 32, 32, sizeof(int) * m, s>>>(ow.pth, ow.ptl, ow.sh, ow.sl, order, w.pos,
+    cert_flag_kernel<<<(m + 31) / 32, 32, 8 * (size_t)m, s>>>(ow.pth, ow.ptl, ow.sh, ow.sl, order, w.pos,
                                                    w.thr, m, w.ctrl, w.dmax, w.flag, w.ccount,
                                                    w.cand);
     note_launch();

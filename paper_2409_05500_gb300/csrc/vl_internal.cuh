@@ -63,7 +63,7 @@ struct PoolSlot {
   void* buf = nullptr;
   size_t buf_cap = 0;
 };
-constexpr int BATCH_STREAMS = 8;
+constexpr int BATCH_STREAMS = 32;
 }  // namespace vl
 
 struct vl_handle_s {
