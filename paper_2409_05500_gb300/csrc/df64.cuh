@@ -46,6 +46,14 @@ __device__ __forceinline__ F2 add(F2 x, F2 y) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// x + y when |x.hi| >= |y.hi| is known (a constant term of a series plus a
+// smaller remainder): FastTwoSum in place of the first TwoSum
+__device__ __forceinline__ F2 add_big(F2 x, F2 y) {
+  F2 s = fast_two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+
 __device__ __forceinline__ F2 neg(F2 x) { return {-x.hi, -x.lo}; }
 
 __device__ __forceinline__ F2 mul(F2 x, F2 y) {
@@ -114,19 +122,25 @@ constexpr float C6 = 0.0013888889225199819f;  // 1/6!
 // staged in shared memory.
 __device__ __forceinline__ F2 dexp(F2 x, const float2* tab) {
   if (x.hi < -87.0f) return {0.0f, 0.0f};
-  const float kf = rintf(__fmul_rn(x.hi, INV_LN2_32));
-  const int k = (int)kf;
+  // k = nearest integer to x 32/ln2: adding 1.5 2^23 leaves the rounded
+  // integer in the low mantissa bits (|x 32/ln2| < 2^22), which avoids the
+  // slower round and float-to-int conversion instructions
+  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+  const float kb = __fmaf_rn(x.hi, INV_LN2_32, kRound);
+  const int k = __float_as_int(kb) - __float_as_int(kRound);
+  const float kf = __fsub_rn(kb, kRound);
   // r = x - k ln2/32: k * hi exactly as a pair, x.hi - p exact (Sterbenz)
   const float p = __fmul_rn(kf, LN2_32_HI);
   const float pe = __fmaf_rn(kf, LN2_32_HI, -p);
   const float t = __fsub_rn(__fsub_rn(x.lo, pe), __fmul_rn(kf, LN2_32_LO));
   const F2 r = two_sum(__fsub_rn(x.hi, p), t);
-  // e^r = 1 + r + r^2/2 + r^3/6 + r^4/24 + r^5/120 + r^6/720
+  // e^r = 1 + r + r^2/2 + r^3/6 + r^4/24 + r^5/120 + r^6/720; with |r| < 0.011
+  // every Horner step adds a remainder smaller than its constant
   const float q = __fmaf_rn(r.hi, __fmaf_rn(r.hi, C6, C5), C4);
-  F2 s = add(F2{C3_HI, C3_LO}, mul_f(r, q));
-  s = add(F2{0.5f, 0.0f}, mul(r, s));
-  s = add(F2{1.0f, 0.0f}, mul(r, s));
-  s = add(F2{1.0f, 0.0f}, mul(r, s));
+  F2 s = add_big(F2{C3_HI, C3_LO}, mul_f(r, q));
+  s = add_big(F2{0.5f, 0.0f}, mul(r, s));
+  s = add_big(F2{1.0f, 0.0f}, mul(r, s));
+  s = add_big(F2{1.0f, 0.0f}, mul(r, s));
   const float2 tj = tab[k & 31];
   s = mul(s, F2{tj.x, tj.y});
   const int m2 = k >> 5;  // floor(k / 32)
@@ -137,7 +151,7 @@ __device__ __forceinline__ F2 dexp(F2 x, const float2* tab) {
 __device__ __forceinline__ F2 dlog1p(F2 y, const float2* tab) {
   const float l0 = log1pf(y.hi);
   const F2 e = dexp(F2{-l0, 0.0f}, tab);  // e^{-l0}
-  F2 z = two_sum(1.0f, y.hi);
+  F2 z = fast_two_sum(1.0f, y.hi);  // y <= 1
   z.lo = __fadd_rn(z.lo, y.lo);
   const F2 q = mul(z, e);  // (1 + y) e^{-l0} = 1 + w
   const float w = __fadd_rn(__fsub_rn(q.hi, 1.0f), q.lo);

@@ -27,7 +27,7 @@
 //      H(x_i) - H(r_j<-i) in FP64.  The per-sample log cosh and u e^{-u^2/2}
 //      agree with FP64 to 3e-14 absolute (measured over 2M samples with light
 //      and heavy tails), six orders of magnitude below the smallest score gap
-//      the decision has to resolve, at a twelfth of the FP64 cost on this part.
+//      the decision has to resolve, at a thirteenth of the FP64 cost on this part.
 //   4. decide: every flagged step recomputes its candidates' exact scores over
 //      its remaining set and takes the argmin (ties: lowest index).  The first
 //      step whose pick changes is resumed: the search restarts there with the
