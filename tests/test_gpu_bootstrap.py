@@ -97,7 +97,18 @@ def _allowed(ref, prec, B):
     return near + amb.sum(), np.full((m, m), float(amb.sum())), int(amb.sum())
 
 
-def _check(vl, h, inst, B, L, seed, prec):
+_refs = {}
+
+
+def _oracle_bootstrap(name, inst, B, L, seed):
+    key = (name, B, L, seed)
+    if key not in _refs:
+        _refs[key] = oracle.bootstrap(inst.X, inst.p, B, L, seed, THRESHOLD)
+    return _refs[key]
+
+
+def _check(vl, h, name, B, L, seed, prec):
+    inst = synth.make_config(name)
     X = torch.from_numpy(inst.X).cuda()
     m = inst.X.shape[0]
     ep = torch.empty((m, m), dtype=torch.float64, device="cuda")
@@ -105,7 +116,7 @@ def _check(vl, h, inst, B, L, seed, prec):
     vl.vl_bootstrap(h, X, inst.p, B, L, seed, THRESHOLD, prec, ep, op)
     h.sync()
     ep, op = ep.cpu().numpy(), op.cpu().numpy()
-    ref = oracle.bootstrap(inst.X, inst.p, B, L, seed, THRESHOLD)
+    ref = _oracle_bootstrap(name, inst, B, L, seed)
     # structure that holds at any size
     off = ~np.eye(m, dtype=bool)
     assert np.all(np.diag(op) == 0) and np.allclose((op + op.T)[off], 1.0)
@@ -127,14 +138,21 @@ def _check(vl, h, inst, B, L, seed, prec):
 def test_bootstrap_pr1_over_two_chunks(vl, h, prec):
     """300 resamples of the 10-variable series: more than one chunk of the
     batched path (256), so the counts carry across chunks."""
-    n_amb = _check(vl, h, synth.make_config("pr1"), 300, 50, 2024, prec)
+    n_amb = _check(vl, h, "pr1", 300, 50, 2024, prec)
     assert n_amb <= 30
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed_certified"])
 def test_bootstrap_fmri(vl, h, prec):
     """16 resamples of the 50-variable, 200-point series in blocks of 20."""
-    _check(vl, h, synth.make_config("fmri"), 16, 20, 31, prec)
+    _check(vl, h, "fmri", 16, 20, 31, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_certified"])
+def test_bootstrap_server_var3(vl, h, prec):
+    """Two resamples of the 120-variable, 10,000-point VAR(3) series in blocks
+    of 500 (the oracle takes several seconds per resample)."""
+    _check(vl, h, "server", 2, 500, 5, prec)
 
 
 def test_bootstrap_single_resample_is_the_fit_of_that_resample(vl, h):
