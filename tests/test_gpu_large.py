@@ -1,6 +1,8 @@
 """GPU parity at full size against stored oracle values: all 256 series of the
 mixed-size batch through vl_fit_batched, and the finance-shaped stretch
-series (m = 800 and 1600, n = 5000) through the step-by-step calls.
+series (m = 800 and 1600, n = 5000) through the step-by-step calls; and the
+ordering above 2048 variables (four per thread) and at the maximum size
+against the oracle's Algorithm 1 on random antisymmetric D.
 
 The stored values (tests/golden/*_oracle.json.gz) were written by
 tests/golden/make_golden.py from the FP64 oracle alone: per series the whole
@@ -143,3 +145,51 @@ def test_stretch_series_against_the_oracle(vl, h, m, prec):
         st = out["cert_stats"].cpu().numpy()
         errs.update(flagged=st[0], pairs=st[1], changed=st[2], unverified=st[3])
     _report(f"stretch m={m} {prec}", **errs)
+
+
+def test_causal_order_four_variables_per_thread(vl):
+    """m = 2100 (above 2048, where the search holds four variables per
+    thread): the whole order equals Algorithm 1's on the same D."""
+    h = vl.Handle(0)
+    try:
+        m = 2100
+        rng = np.random.default_rng(2100)
+        A = rng.normal(size=(m, m))
+        D = A - A.T
+        order = torch.empty(m, dtype=torch.int32, device="cuda")
+        vl.vl_causal_order(h, torch.from_numpy(D).cuda(), order)
+        h.sync()
+        ref = oracle.order_heuristic(D)
+        assert [int(c) for c in order.cpu().numpy()] == [int(c) for c in ref["order"]]
+    finally:
+        h.close()
+
+
+def test_causal_order_at_the_maximum_size(vl):
+    """m = VL_MAX_M = 4096 (the oracle's whole search would take minutes):
+    the order is a permutation, and at the first 10 and the last 300 steps,
+    walked over the GPU's own remaining sets, the pick minimises the oracle's
+    scores of Eq. 3 (or lies within 1e-6 relative of the minimum)."""
+    h = vl.Handle(0)
+    try:
+        m = 4096
+        rng = np.random.default_rng(4096)
+        A = rng.normal(size=(m, m))
+        D = A - A.T
+        order_t = torch.empty(m, dtype=torch.int32, device="cuda")
+        vl.vl_causal_order(h, torch.from_numpy(D).cuda(), order_t)
+        h.sync()
+        order = [int(c) for c in order_t.cpu().numpy()]
+        assert sorted(order) == list(range(m))
+        left = np.ones(m, dtype=bool)
+        checked = 0
+        for k, c in enumerate(order):
+            if k < 10 or k >= m - 300:
+                scores = oracle.scores_over(D, np.nonzero(left)[0])
+                smin = min(scores.values())
+                assert scores[c] - smin <= GAP * max(abs(smin), abs(scores[c]), 1e-300), k
+                checked += 1
+            left[c] = False
+        assert checked == 310
+    finally:
+        h.close()
