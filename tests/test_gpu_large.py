@@ -2,7 +2,8 @@
 mixed-size batch through vl_fit_batched, and the finance-shaped stretch
 series (m = 800 and 1600, n = 5000) through the step-by-step calls; and the
 ordering above 2048 variables (four per thread) and at the maximum size
-against the oracle's Algorithm 1 on random antisymmetric D.
+against the oracle's Algorithm 1 on random antisymmetric D, and the
+pairwise measure at the maximum size on sampled pairs.
 
 The stored values (tests/golden/*_oracle.json.gz) were written by
 tests/golden/make_golden.py from the FP64 oracle alone: per series the whole
@@ -191,5 +192,43 @@ def test_causal_order_at_the_maximum_size(vl):
                 checked += 1
             left[c] = False
         assert checked == 310
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_pairwise_measure_at_the_maximum_size(vl, prec):
+    """m = VL_MAX_M = 4096 variables, n = 300 samples (a ragged sample tail):
+    every variable entropy against the oracle's, and D at 300 seeded pairs,
+    each computed by the oracle from its own residual (within D_REL of the
+    largest |D| of the whole matrix, taken from the GPU's D since the
+    oracle's is too large to form here; H within H_REL of max(|H|, H_nu))."""
+    h = vl.Handle(0)
+    try:
+        m, n = 4096, 300
+        rng = np.random.default_rng(43)
+        E = rng.laplace(size=(m, n))
+        E[1:] += 0.4 * E[:-1]
+        Et = torch.from_numpy(E).cuda()
+        f64 = dict(dtype=torch.float64, device="cuda")
+        Hx, Hr, D = torch.empty(m, **f64), torch.empty((m, m), **f64), torch.empty((m, m), **f64)
+        vl.vl_pairwise_measure(h, Et, prec, Hx, Hr, D)
+        h.sync()
+        Hx, D = Hx.cpu().numpy(), D.cpu().numpy()
+        Xs = oracle.standardize(E)
+        ex = np.array([oracle.entropy(Xs[i]) for i in range(m)])
+        assert np.max(np.abs(Hx - ex) / np.maximum(np.abs(ex), oracle.H_GAUSS)) <= H_REL
+        pairs = rng.choice(m, size=(300, 2))
+        pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+        ref, got = [], []
+        for i, j in pairs:
+            rij = oracle.residual(Xs[i], Xs[j])
+            rji = oracle.residual(Xs[j], Xs[i])
+            ref.append(ex[j] + oracle.entropy(rij / rij.std()) - ex[i]
+                       - oracle.entropy(rji / rji.std()))
+            got.append(D[i, j])
+        ref, got = np.array(ref), np.array(got)
+        assert np.max(np.abs(got - ref)) <= D_REL * np.max(np.abs(D))
+        assert np.allclose(D, -D.T, atol=1e-15 + 1e-12 * np.max(np.abs(D)))
     finally:
         h.close()
