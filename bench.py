@@ -15,10 +15,10 @@ per step, pair-samples = m (m - 1) / 2 * (n - p).  The L2 cache is flushed
 --impl reference times the CPU FP64 oracle (the plain restatement of the
 paper) on a bounded sample of the same workload, on this host's cores.
 
-Besides the headline, the line carries (each skippable by a --no-* flag): the
-plain FP64 GPU step, the certified step, the iterative search of Sec. 3 on
-the same residuals, the 256-series mixed-size batch, and a 64-resample
-moving-block bootstrap of the workload.
+Besides the headline, the line carries (all but the certified step can be
+skipped with a --no-* flag): the plain FP64 GPU step, the certified step, the
+iterative search of Sec. 3 on the same residuals, the 256-series mixed-size
+batch, and a 64-resample moving-block bootstrap of the workload.
 """
 from __future__ import annotations
 
